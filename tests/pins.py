@@ -1,0 +1,329 @@
+"""Pins for the oracle: checks against facts fixed by the mathematics, not by
+the oracle itself.  Each ``pin_*`` takes an oracle library handle (the real one
+or a deliberately broken build, see test_oracle_mutants.py) and returns
+``(ok, worst_error)``.
+
+Sources of truth used here (none of them re-types an oracle formula):
+  * LAPACK via numpy.linalg.solve on the assembled dense matrix;
+  * exact rational Gaussian elimination (fractions.Fraction) on tiny systems;
+  * eigenvectors of constant-coefficient (Toeplitz) tridiagonal matrices;
+  * manufactured solutions d = A x* (the definition of the problem);
+  * the discrete heat-equation eigenmode decay factor of the ADI step;
+  * dense Kronecker-product assembly of one ADI step on a tiny mesh;
+  * the transpose identity <A^{-1} d, g> = <d, A^{-T} g> and central finite
+    differences for the adjoint.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+from paper_2201_03950_gb300 import inputs
+
+
+def dense_matrix(a, b, c):
+    """Assemble the N x N matrix of eq. tdma-system (a_0, c_{N-1} dropped)."""
+    n = len(b)
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, i] = b[i]
+        if i > 0:
+            A[i, i - 1] = a[i]
+        if i < n - 1:
+            A[i, i + 1] = c[i]
+    return A
+
+
+def rel(x, ref):
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = max(np.max(np.abs(ref)), 1e-300)
+    return float(np.max(np.abs(x - ref)) / scale)
+
+
+def _random_dominant(n, seed):
+    a, b, c, d = inputs.dominant_system((n,), seed=seed, dtype=np.float64)
+    return a, b, c, d
+
+
+SOLVERS = {
+    "thomas": lambda lib, a, b, c, d: oracle.thomas(a, b, c, d, lib=lib),
+    "pcr": lambda lib, a, b, c, d: oracle.pcr(a, b, c, d, lib=lib),
+    "tiled_thomas_m3": lambda lib, a, b, c, d: oracle.tiled(a, b, c, d, 3, False, lib=lib),
+    "tiled_pcr_m4": lambda lib, a, b, c, d: oracle.tiled(a, b, c, d, 4, True, lib=lib),
+    "tiled_thomas_m8": lambda lib, a, b, c, d: oracle.tiled(a, b, c, d, 8, False, lib=lib),
+    "tiled_pcr_m16": lambda lib, a, b, c, d: oracle.tiled(a, b, c, d, 16, True, lib=lib),
+}
+
+
+def pin_lapack(lib, tol=1e-12):
+    """P1: every solver against LAPACK on random dominant systems, N <= 70,
+    with garbage in the unread a_0 / c_{N-1} slots."""
+    worst = 0.0
+    for n in (1, 2, 3, 4, 5, 7, 8, 9, 17, 31, 33, 50, 53, 64, 70):
+        a, b, c, d = _random_dominant(n, seed=100 + n)
+        ref = np.linalg.solve(dense_matrix(a, b, c), d)
+        a = a.copy(); c = c.copy()
+        a[0] = 123.0
+        c[-1] = -77.0
+        for fn in SOLVERS.values():
+            worst = max(worst, rel(fn(lib, a, b, c, d), ref))
+        worst = max(worst, rel(oracle.dense_solve(dense_matrix(a, b, c), d, lib=lib), ref))
+    return worst <= tol, worst
+
+
+def pin_dense_general(lib, tol=1e-11):
+    """Dense Gaussian elimination with pivoting against LAPACK on general
+    (non-tridiagonal, pivoting-requiring) matrices."""
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for n in (1, 2, 3, 6, 11, 20):
+        A = rng.standard_normal((n, n))
+        A[0, 0] = 0.0  # forces a row exchange
+        if n == 1:
+            A[0, 0] = 0.5
+        rhs = rng.standard_normal(n)
+        worst = max(worst, rel(oracle.dense_solve(A, rhs, lib=lib), np.linalg.solve(A, rhs)))
+    return worst <= tol, worst
+
+
+def _exact_solve(a, b, c, d):
+    """Gaussian elimination in exact rational arithmetic (brute force)."""
+    n = len(b)
+    M = [[Fraction(0)] * n for _ in range(n)]
+    for i in range(n):
+        M[i][i] = Fraction(b[i])
+        if i > 0:
+            M[i][i - 1] = Fraction(a[i])
+        if i < n - 1:
+            M[i][i + 1] = Fraction(c[i])
+    y = [Fraction(v) for v in d]
+    for k in range(n):
+        p = next(r for r in range(k, n) if M[r][k] != 0)
+        M[k], M[p] = M[p], M[k]
+        y[k], y[p] = y[p], y[k]
+        for r in range(k + 1, n):
+            f = M[r][k] / M[k][k]
+            for j in range(k, n):
+                M[r][j] -= f * M[k][j]
+            y[r] -= f * y[k]
+    x = [Fraction(0)] * n
+    for k in range(n - 1, -1, -1):
+        s = y[k] - sum(M[k][j] * x[j] for j in range(k + 1, n))
+        x[k] = s / M[k][k]
+    return [float(v) for v in x]
+
+
+def pin_exact_rational(lib, tol=1e-14):
+    """Brute force: small-integer systems solved exactly with fractions."""
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for n in (1, 2, 3, 4, 6, 9, 12):
+        a = rng.integers(-3, 4, n).astype(np.float64)
+        c = rng.integers(-3, 4, n).astype(np.float64)
+        b = np.abs(a) + np.abs(c) + rng.integers(1, 4, n)
+        b *= np.where(rng.random(n) < 0.5, -1.0, 1.0)  # mixed signs, still dominant
+        d = rng.integers(-9, 10, n).astype(np.float64)
+        ref = _exact_solve([0] + list(a[1:]), b, list(c[:-1]) + [0], d)
+        for fn in SOLVERS.values():
+            worst = max(worst, rel(fn(lib, a, b, c, d), ref))
+    return worst <= tol, worst
+
+
+def pin_toeplitz(lib, tol=1e-12):
+    """P2: constant a, b, c.  v_j = rho^j sin((j+1) k pi/(n+1)), rho =
+    sqrt(a/c), is an eigenvector with eigenvalue b + 2 s cos(k pi/(n+1)),
+    s = sign(a) sqrt(a c); so d = v gives x = v / eigenvalue exactly."""
+    worst = 0.0
+    cases = [(-0.4, 2.0, -0.4), (0.3, 1.1, 0.3), (-0.2, 1.5, -0.6), (0.7, -2.5, 0.25)]
+    for (av, bv, cv) in cases:
+        for n in (1, 2, 5, 16, 33, 64):
+            for k in sorted({1, 2, (n + 1) // 2, n}):
+                if k < 1 or k > n:
+                    continue
+                th = k * math.pi / (n + 1)
+                rho = math.sqrt(av / cv)
+                s = math.copysign(math.sqrt(av * cv), av)
+                j = np.arange(n)
+                v = rho ** j * np.sin((j + 1) * th)
+                lam = bv + 2.0 * s * math.cos(th)
+                a = np.full(n, av); b = np.full(n, bv); c = np.full(n, cv)
+                for fn in SOLVERS.values():
+                    worst = max(worst, rel(fn(lib, a, b, c, v), v / lam))
+    return worst <= tol, worst
+
+
+def pin_manufactured(lib, tol=1e-12):
+    """P3: draw x*, form d = A x* from the problem's definition, recover x*."""
+    worst = 0.0
+    rng = np.random.default_rng(5)
+    for n in (3, 10, 100, 257, 1000):
+        a, b, c, _ = _random_dominant(n, seed=300 + n)
+        xs = rng.uniform(-1, 1, n)
+        d = b * xs
+        d[1:] += a[1:] * xs[:-1]
+        d[:-1] += c[:-1] * xs[1:]
+        for fn in SOLVERS.values():
+            worst = max(worst, rel(fn(lib, a, b, c, d), xs))
+    return worst <= tol, worst
+
+
+def pin_mesh(lib, tol=1e-12):
+    """Mesh solves: each axis against LAPACK on every line; accumulate adds;
+    the unread first-a / last-c of each line may hold NaN."""
+    worst = 0.0
+    dims = (5, 4, 3)
+    tot = 60
+    a, b, c, d = inputs.dominant_system((tot,), seed=9, dtype=np.float64)
+    strides = (1, 5, 20)
+    for k in range(3):
+        n, st = dims[k], strides[k]
+        aa = a.copy(); cc = c.copy()
+        x_ref = np.zeros(tot)
+        others = [ax for ax in range(3) if ax != k]
+        for j2 in range(dims[others[1]]):
+            for j1 in range(dims[others[0]]):
+                base = j1 * strides[others[0]] + j2 * strides[others[1]]
+                idx = base + st * np.arange(n)
+                aa[idx[0]] = np.nan
+                cc[idx[-1]] = np.nan
+                x_ref[idx] = np.linalg.solve(dense_matrix(a[idx], b[idx], c[idx]), d[idx])
+        x = oracle.solve_mesh(aa, b, cc, d, dims, k, lib=lib)
+        worst = max(worst, rel(x, x_ref))
+        u0 = np.linspace(-1, 1, tot)
+        u = u0.copy()
+        oracle.solve_mesh(aa, b, cc, d, dims, k, out=u, lib=lib)
+        worst = max(worst, rel(u - u0, x_ref))
+    return worst <= tol, worst
+
+
+def _mu(p, n):
+    return -4.0 * math.sin(math.pi * p / (2.0 * (n - 1))) ** 2
+
+
+def pin_adi_eigenmode(lib, tol=1e-11):
+    """P5: u = prod sin(pi k_ax i / (n_ax - 1)) is an eigenvector of the
+    stencil and of every directional operator, so one ADI step multiplies it by
+    g = 1 + lam sum(mu) / prod(1 - lam mu),  mu = -4 sin^2(pi k / (2(n-1))).
+    A sum of modes decays mode by mode."""
+    worst = 0.0
+    for dims, lam, steps in (((9, 7, 6), 0.1, 5), ((12, 10), 0.3, 7), ((17, 17, 17), 0.1, 3)):
+        modes = inputs.sine_modes(dims, seed=len(dims), nmodes=3)
+        u0 = inputs.sine_field(dims, modes)
+        ref = np.zeros_like(u0)
+        for ks, amp in modes:
+            mus = [_mu(k, n) for k, n in zip(ks, dims)]
+            g = 1.0 + lam * sum(mus) / np.prod([1.0 - lam * m for m in mus])
+            ref += inputs.sine_field(dims, [(ks, amp * g ** steps)])
+        worst = max(worst, rel(oracle.adi(u0, dims, lam, steps, lib=lib), ref))
+    return worst <= tol, worst
+
+
+def _axis_op(n, lam):
+    T = np.eye(n)
+    for i in range(1, n - 1):
+        T[i, i - 1] = -lam
+        T[i, i] = 1 + 2 * lam
+        T[i, i + 1] = -lam
+    return T
+
+
+def pin_adi_dense(lib, tol=1e-12):
+    """One ADI step on a tiny random mesh assembled as dense Kronecker
+    products: Delta = Z^{-1} Y^{-1} X^{-1} (lam L u restricted to the interior),
+    u' = u + Delta, with L the 2*ndim-neighbour Laplacian."""
+    worst = 0.0
+    rng = np.random.default_rng(3)
+    for dims, lam in (((5, 6, 4), 0.2), ((6, 5), 0.15)):
+        nd = len(dims)
+        tot = int(np.prod(dims))
+        u = rng.uniform(-1, 1, tot)
+        grid = np.indices(tuple(reversed(dims))).reshape(nd, -1)[::-1]
+        interior = np.ones(tot, dtype=bool)
+        for ax in range(nd):
+            interior &= (grid[ax] > 0) & (grid[ax] < dims[ax] - 1)
+        u[~interior] = 0.0
+        # Laplacian by explicit neighbour sums
+        U = u.reshape(tuple(reversed(dims)))
+        rhs = np.zeros_like(U)
+        inner = tuple(slice(1, -1) for _ in range(nd))
+        acc = -2.0 * nd * U[inner]
+        for ax in range(nd):
+            arr_ax = nd - 1 - ax
+            for sh in (-1, 1):
+                sl = [slice(1, -1)] * nd
+                sl[arr_ax] = slice(1 + sh, U.shape[arr_ax] - 1 + sh)
+                acc = acc + U[tuple(sl)]
+        rhs[inner] = lam * acc
+        rhs = rhs.reshape(-1)
+        # x-operator acts on the contiguous index -> kron(I_z, I_y, X)
+        ops = [_axis_op(n, lam) for n in dims]
+        full = np.eye(1)
+        mats = []
+        for ax in range(nd):
+            factors = [np.eye(dims[k]) if k != ax else ops[k] for k in range(nd)]
+            M = np.eye(1)
+            for f in reversed(factors):
+                M = np.kron(M, f)
+            mats.append(M)
+        delta = rhs
+        for M in mats:
+            delta = np.linalg.solve(M, delta)
+        ref = u + delta
+        worst = max(worst, rel(oracle.adi(u, dims, lam, 1, lib=lib), ref))
+        del full
+    return worst <= tol, worst
+
+
+def pin_varlen(lib, tol=1e-12):
+    lengths = [1, 2, 3, 17, 5, 64]
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    a, b, c, d = inputs.dominant_system((int(off[-1]),), seed=21, dtype=np.float64)
+    x = oracle.solve_varlen(a, b, c, d, off, lib=lib)
+    worst = 0.0
+    for k in range(len(lengths)):
+        s, e = off[k], off[k + 1]
+        ref = np.linalg.solve(dense_matrix(a[s:e], b[s:e], c[s:e]), d[s:e])
+        worst = max(worst, rel(x[s:e], ref))
+    return worst <= tol, worst
+
+
+def pin_adjoint(lib, tol=1e-7):
+    """Adjoint: g_d against LAPACK on A^T (tight), the dot-product identity,
+    and g_a, g_b, g_c, g_d against central differences of L = <g, x(a,b,c,d)>."""
+    worst_tight = 0.0
+    worst_fd = 0.0
+    rng = np.random.default_rng(17)
+    for n in (1, 2, 5, 12):
+        a, b, c, d = _random_dominant(n, seed=400 + n)
+        g = rng.uniform(-1, 1, n)
+        A = dense_matrix(a, b, c)
+        x = np.linalg.solve(A, d)
+        ga, gb, gc, gd = oracle.adjoint(a, b, c, x, g, lib=lib)
+        worst_tight = max(worst_tight, rel(gd, np.linalg.solve(A.T, g)))
+        lhs = float(np.dot(x, g))
+        rhs_ = float(np.dot(d, gd))
+        worst_tight = max(worst_tight, abs(lhs - rhs_) / max(abs(lhs), 1e-30))
+        h = 1e-6
+
+        def loss(aa, bb, cc, dd):
+            return float(np.dot(np.linalg.solve(dense_matrix(aa, bb, cc), dd), g))
+
+        for arr_i, grad in ((0, ga), (1, gb), (2, gc), (3, gd)):
+            fd = np.zeros(n)
+            for i in range(n):
+                args_p = [v.copy() for v in (a, b, c, d)]
+                args_m = [v.copy() for v in (a, b, c, d)]
+                args_p[arr_i][i] += h
+                args_m[arr_i][i] -= h
+                fd[i] = (loss(*args_p) - loss(*args_m)) / (2 * h)
+            worst_fd = max(worst_fd, float(np.max(np.abs(fd - grad))))
+    ok = worst_tight <= 1e-12 and worst_fd <= tol
+    return ok, max(worst_tight, worst_fd)
+
+
+ALL_PINS = [pin_lapack, pin_dense_general, pin_exact_rational, pin_toeplitz, pin_manufactured,
+            pin_mesh, pin_adi_eigenmode, pin_adi_dense, pin_varlen, pin_adjoint]

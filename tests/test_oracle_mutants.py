@@ -1,0 +1,57 @@
+"""The pins must be sharp: each plausible mistake planted in a copy of the
+oracle source (on the CPU, in a temporary build) must fail at least one pin.
+The real oracle source is never modified."""
+import os
+
+import pytest
+
+import oracle
+import pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "trid_oracle.c")
+
+# (name, original text, planted mistake)
+MUTANTS = [
+    ("thomas_forward_sign", "ds[i] = r * (d[i] - a[i] * ds[i - 1]);",
+     "ds[i] = r * (d[i] + a[i] * ds[i - 1]);"),
+    ("thomas_backward_sign", "x[i] = ds[i] - cs[i] * x[i + 1];", "x[i] = ds[i] + cs[i] * x[i + 1];"),
+    ("thomas_pivot_index", "double den = b[i] - a[i] * cs[i - 1];",
+     "double den = b[i] - a[i] * cs[i > 1 ? i - 2 : 0];"),
+    ("pcr_transposed_operand", "am = A0[i - s]; cm = C0[i - s];", "am = C0[i - s]; cm = A0[i - s];"),
+    ("pcr_sign", "double den = 1.0 - A0[i] * cm - C0[i] * ap;",
+     "double den = 1.0 - A0[i] * cm + C0[i] * ap;"),
+    ("pcr_rounds", "while (((int64_t)1 << P) < n) ++P;", "while (((int64_t)2 << P) < n) ++P;"),
+    ("tiled_dropped_term", "ah[i] = ah[i] - ch[i] * ah[i + 1];", "ah[i] = ah[i];"),
+    ("tiled_reduced_diag", "rb[2 * k] = 1.0 - ch[s] * ah[s + 1];", "rb[2 * k] = 1.0;"),
+    ("mesh_accumulate", "if (accumulate) out[p] += lx[i]; else out[p] = lx[i];", "out[p] = lx[i];"),
+    ("adi_stencil_centre", "dd[p] = lambda * (s - 2.0 * ndim * u[p]);", "dd[p] = lambda * (s - ndim * u[p]);"),
+    ("adi_operator_diag", "lb[i] = bnd ? 1.0 : 1.0 + 2.0 * lambda;", "lb[i] = bnd ? 1.0 : 1.0 + lambda;"),
+    ("adi_missing_z", "if (ndim == 3) s += u[p - stride[2]] + u[p + stride[2]];",
+     "if (ndim == 4) s += u[p - stride[2]] + u[p + stride[2]];"),
+    ("adjoint_not_transposed", "ta[i] = (i == 0) ? 0.0 : c[i - 1];", "ta[i] = (i == 0) ? 0.0 : a[i];"),
+    ("adjoint_wrong_neighbour", "gc[i] = (i == n - 1) ? 0.0 : -gd[i] * x[i + 1];",
+     "gc[i] = (i == n - 1) ? 0.0 : -gd[i] * x[i];"),
+    ("dense_no_pivoting", "if (v > best) { best = v; piv = r; }", "if (0) { best = v; piv = r; }"),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, orig, bad):
+    text = open(SRC).read()
+    assert text.count(orig) == 1, f"mutation site for {name} not unique/present"
+    src = tmp_path / "mutant.c"
+    src.write_text(text.replace(orig, bad))
+    so = str(tmp_path / "libmutant.so")
+    import subprocess
+    subprocess.run(["gcc", *oracle.CFLAGS, str(src), "-o", so, "-lm"], check=True)
+    lib = oracle.load(so)
+    failed = []
+    for pin in pins.ALL_PINS:
+        try:
+            ok, _ = pin(lib)
+        except (ZeroDivisionError, ValueError, FloatingPointError, OverflowError,
+                __import__("numpy").linalg.LinAlgError):
+            ok = False
+        if not ok:
+            failed.append(pin.__name__)
+    assert failed, f"planted mistake {name} passed every pin"
