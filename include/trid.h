@@ -1,0 +1,141 @@
+/*
+ * trid.h -- C ABI of the GB300 (sm_103a) batched tridiagonal solver and ADI
+ * heat-diffusion step.
+ *
+ * Method: arXiv 2201.03950, "High Throughput Multidimensional Tridiagonal
+ * Systems Solvers on FPGAs".  The problem statement is Section 2, eq.
+ * tdma-single / tdma-system:
+ *
+ *     a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i,   i = 0..N-1,
+ *     a_0 = c_{N-1} = 0,
+ *
+ * with many independent systems laid along one axis of a 2D/3D mesh
+ * (Section 2.1).  Meshes are column-major: element (i0, i1, i2) of a mesh with
+ * dims (n0, n1, n2) sits at linear index i0 + n0 * (i1 + n1 * i2), so dims[0]
+ * is the contiguous (x) axis.
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named a, b, c, d, u, workspace are DEVICE pointers owned by the
+ *     caller; the library never frees or retains them.  Dense, packed arrays
+ *     of prod(dims) elements of the given dtype.  Any element-aligned address
+ *     is accepted; 16-byte alignment enables vector loads.
+ *   - `dims` and `offsets` marked "host" are read on the host during the call.
+ *   - Argument errors are detected on the host before any launch: the call
+ *     returns a nonzero trid_status and launches nothing.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream).  A launch failure reported by the runtime right
+ *     after the launch maps to TRID_ERR_CUDA.
+ *   - No exception, abort() or exit() crosses this ABI.
+ *   - Every call may be captured into a CUDA graph, EXCEPT the first call on a
+ *     device (which queries device attributes) and calls that need to grow
+ *     the library's scratch pool (see trid_solve_batch).
+ */
+#ifndef TRID_H_
+#define TRID_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *trid_stream_t; /* identical to cudaStream_t */
+
+typedef enum { TRID_F32 = 0, TRID_F64 = 1 } trid_dtype;
+
+typedef enum {
+    TRID_OK = 0,
+    TRID_ERR_INVALID_ARG = 1, /* NULL pointer, bad dims/ndim/solve_dim/dtype, aliasing */
+    TRID_ERR_UNSUPPORTED = 2, /* valid request this build cannot serve          */
+    TRID_ERR_MISALIGNED = 3,  /* pointer not aligned to its element size        */
+    TRID_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed           */
+    TRID_ERR_ALLOC = 5,       /* scratch allocation failed / workspace too small */
+    TRID_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up             */
+} trid_status;
+
+/* Human-readable name of a status code (static storage). */
+const char *trid_status_string(trid_status s);
+
+/*
+ * Batched solve along one mesh axis (Section 2.1; Algorithm "thomas" of
+ * Section 2 defines the result, which is the unique x = A^{-1} d).
+ *
+ *   dims[0..ndim-1]  host int64 mesh extents, ndim in {1, 2, 3}, each >= 0.
+ *   solve_dim        axis along which the systems lie, 0 <= solve_dim < ndim.
+ *                    There are prod(dims)/dims[solve_dim] systems of length
+ *                    dims[solve_dim]; element i of a system is i * stride
+ *                    after its first element (stride 1, n0 or n0*n1).
+ *   a, b, c          coefficients; a at the first element and c at the last
+ *                    element of every system are NOT read (treated as 0).
+ *   d                right-hand side.
+ *   u == NULL        x overwrites d in place (the listing's "update d").
+ *   u != NULL        u += x and d is left unmodified (Algorithm "adi",
+ *                    "u = u + d").  u must not alias a, b, c or d.
+ *   dtype            TRID_F32 or TRID_F64; all arrays share it.
+ *
+ * Systems longer than the on-chip limit of the single-pass kernels (256 in
+ * this build) are solved with the tiled Thomas-PCR hybrid of Section 3.1 in
+ * several passes; those passes need scratch of
+ * trid_solve_workspace_bytes(...) bytes, which this entry point takes from a
+ * library-owned pool (grown with cudaMalloc on first need; that first call
+ * must not be inside a stream capture).  Use trid_solve_batch_ws to pass
+ * caller-owned scratch instead.
+ * No numerical pivoting: the caller guarantees a nonsingular system for
+ * which Gaussian elimination without pivoting is stable (e.g. diagonally
+ * dominant rows).  An exact zero pivot yields inf/nan, not an error code.
+ */
+trid_status trid_solve_batch(const void *a, const void *b, const void *c, void *d, void *u,
+                             const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
+                             trid_stream_t stream);
+
+/* Scratch bytes trid_solve_batch_ws needs for this problem (0 when the
+ * single-pass kernels serve it).  Returns 0 as well for invalid arguments. */
+size_t trid_solve_workspace_bytes(const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype);
+
+/* As trid_solve_batch, with caller-owned device scratch `workspace` of
+ * `workspace_bytes` bytes (>= trid_solve_workspace_bytes; 256-byte aligned).
+ * Never allocates.  Returns TRID_ERR_ALLOC if the workspace is too small. */
+trid_status trid_solve_batch_ws(const void *a, const void *b, const void *c, void *d, void *u,
+                                const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
+                                void *workspace, size_t workspace_bytes, trid_stream_t stream);
+
+/*
+ * ADI heat-diffusion time steps, Section 4.1, Algorithm "adi": per step,
+ * d = lambda * (sum of the 2*ndim axis neighbours of u - 2*ndim*u) on interior
+ * nodes (0 on boundary nodes); d <- X^{-1} d; d <- Y^{-1} d; [d <- Z^{-1} d;]
+ * u <- u + d.  Each directional operator is tridiag(-lambda, 1 + 2 lambda,
+ * -lambda) on interior rows with identity rows at the two Dirichlet-zero
+ * boundary nodes; the coefficients are generated inside the kernels and never
+ * stored (Section 4.1: coefficient generation fused with the solver).
+ *
+ *   u          device array of prod(dims) elements, advanced in place by
+ *              `nsteps` steps.  Boundary nodes must hold 0 and are left 0.
+ *   dims       host int64 extents, ndim in {2, 3}, every extent >= 3.
+ *   lambda     diffusion number, > 0.
+ *   workspace  caller-owned device scratch of at least
+ *              adi_workspace_bytes(dims, ndim, dtype) bytes, 256-byte aligned.
+ */
+trid_status adi_step(void *u, const int64_t *dims, int ndim, double lambda, int nsteps,
+                     trid_dtype dtype, void *workspace, size_t workspace_bytes,
+                     trid_stream_t stream);
+
+/* Scratch size adi_step needs: one mesh-sized array (the intermediate d of
+ * the two-pass schedule) plus alignment.  0 for invalid arguments. */
+size_t adi_workspace_bytes(const int64_t *dims, int ndim, trid_dtype dtype);
+
+/*
+ * Device status word: kernels that run a bounded wait, or debug bounds
+ * checks, record the first failure here instead of trapping.  This call
+ * synchronises `stream`, returns TRID_OK or the recorded failure
+ * (TRID_ERR_TIMEOUT, TRID_ERR_INVALID_ARG) and clears the word.
+ */
+trid_status trid_get_device_status(trid_stream_t stream);
+
+/* Library version string (static storage). */
+const char *trid_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRID_H_ */

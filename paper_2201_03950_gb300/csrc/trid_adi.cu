@@ -1,0 +1,234 @@
+// trid_adi.cu -- ADI heat-diffusion step (arXiv 2201.03950, Section 4.1,
+// Algorithm "adi") with the coefficients generated inside the kernels.
+//
+// One step, delta form, Dirichlet-zero boundary:
+//   d = lambda * (sum of axis neighbours - 2*ndim*u)   (interior; 0 on boundary)
+//   d <- X^{-1} d ; d <- Y^{-1} d ; [d <- Z^{-1} d] ; u <- u + d
+// with X, Y, Z = tridiag(-lambda, 1 + 2 lambda, -lambda) on interior rows and
+// identity rows at the boundary nodes.
+//
+// Schedule (three kernels per 3D step, two per 2D step):
+//   k_adi_x_rhs : stencil RHS + x solve, u -> w          (reads u, writes w)
+//   k_strided   : y solve in place on w                  (reads w, writes w)
+//   k_strided   : z solve, u += result                   (reads w, u; writes u)
+#include "trid_device.cuh"
+#include "trid_strided.cuh"
+#include "../../include/trid.h"
+#include "trid_internal.h"
+
+namespace trid {
+
+constexpr int ADI_M = 8;
+constexpr int ADI_MAX_N = 32 * ADI_M;
+
+template <typename T, int M>
+__device__ __forceinline__ void adi_load_tile(const T *__restrict__ p, int64_t i0, int64_t n,
+                                              bool vec, T (&r)[M]) {
+    if (vec && i0 + M <= n) {
+        load_contig_vec<T, M>(p + i0, r);
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; ++j) r[j] = (i0 + j < n) ? p[i0 + j] : T(0);
+    }
+}
+
+// RHS stencil fused with the x solve.  Lines along x are contiguous; G lanes
+// of a warp share a line, lane g owning x in [g*M, g*M + M).
+template <typename T, int M, int G>
+__global__ void __launch_bounds__(256)
+k_adi_x_rhs(const T *__restrict__ u, T *__restrict__ w, int64_t nx, int64_t ny, int64_t nz,
+            int ndim, T lam, int vec_ok) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int g = lane % G;
+    const int64_t line = warp * (32 / G) + lane / G;
+    const int64_t nlines = ny * nz;
+    const bool active = line < nlines;
+    const int64_t y = active ? line % ny : 0;
+    const int64_t z = active ? line / ny : 0;
+    const bool interior = active && y > 0 && y < ny - 1 && (ndim == 2 || (z > 0 && z < nz - 1));
+    const int64_t base = line * nx;
+    const int64_t i0 = int64_t(g) * M;
+    const bool vec = vec_ok != 0;
+
+    T uc[M];
+    if (active) adi_load_tile<T, M>(u + base, i0, nx, vec, uc);
+    else {
+#pragma unroll
+        for (int j = 0; j < M; ++j) uc[j] = T(0);
+    }
+    constexpr unsigned FULL = 0xffffffffu;
+    const T left = __shfl_up_sync(FULL, uc[M - 1], 1, G);
+    const T right = __shfl_down_sync(FULL, uc[0], 1, G);
+
+    T ra[M], rb[M], rc[M], rd[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const int64_t i = i0 + j;
+        const bool in_x = i > 0 && i < nx - 1;
+        ra[j] = in_x ? -lam : T(0);
+        rb[j] = (i < nx && in_x) ? T(1) + T(2) * lam : T(1);
+        rc[j] = in_x ? -lam : T(0);
+        rd[j] = T(0);
+    }
+    if (interior) {
+        T s[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const T xm = (j == 0) ? left : uc[j - 1];
+            const T xp = (j == M - 1) ? right : uc[j + 1];
+            s[j] = xm + xp;
+        }
+        T nb[M];
+        adi_load_tile<T, M>(u + base - nx, i0, nx, vec, nb);
+#pragma unroll
+        for (int j = 0; j < M; ++j) s[j] += nb[j];
+        adi_load_tile<T, M>(u + base + nx, i0, nx, vec, nb);
+#pragma unroll
+        for (int j = 0; j < M; ++j) s[j] += nb[j];
+        if (ndim == 3) {
+            adi_load_tile<T, M>(u + base - nx * ny, i0, nx, vec, nb);
+#pragma unroll
+            for (int j = 0; j < M; ++j) s[j] += nb[j];
+            adi_load_tile<T, M>(u + base + nx * ny, i0, nx, vec, nb);
+#pragma unroll
+            for (int j = 0; j < M; ++j) s[j] += nb[j];
+        }
+        const T centre = T(2 * ndim);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const int64_t i = i0 + j;
+            rd[j] = (i > 0 && i < nx - 1) ? lam * (s[j] - centre * uc[j]) : T(0);
+        }
+    }
+    T as, cs, ds, ae, ce, de, xs, xe;
+    tile_reduce<T, M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
+    group_solve<T, G>(as, cs, ds, ae, ce, de, g, xs, xe);
+    tile_substitute<T, M>(ra, rc, rd, xs, xe);
+    if (!active) return;
+    if (vec && i0 + M <= nx) {
+        store_contig_vec<T, M>(w + base + i0, rd);
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            if (i0 + j < nx) w[base + i0 + j] = rd[j];
+    }
+}
+
+static int pow2_at_least(int64_t v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <typename T, int G>
+static void launch_x_rhs(const T *u, T *w, const int64_t *n3, int ndim, T lam, int vec,
+                         cudaStream_t st) {
+    const int64_t lines = n3[1] * n3[2];
+    const int64_t warps = (lines + (32 / G) - 1) / (32 / G);
+    const int64_t blocks = (warps + 7) / 8;
+    k_adi_x_rhs<T, ADI_M, G><<<dim3(unsigned(blocks)), 256, 0, st>>>(u, w, n3[0], n3[1], n3[2],
+                                                                      ndim, lam, vec);
+}
+
+template <typename T, int NT>
+static void launch_adi_strided(T lam, const T *d, T *out, int acc, const Lines &L,
+                               cudaStream_t st) {
+    // at least one full warp per block: the reduced solve shuffles over all 32 lanes
+    constexpr int SG = (NT * SysCfg<T>::SG < 32) ? 32 / NT : SysCfg<T>::SG;
+    const int64_t blocks = (L.nsys + SG - 1) / SG;
+    AdiCoef<T> coef{lam};
+    k_strided<T, ADI_M, NT, SG, AdiCoef<T>>
+        <<<dim3(unsigned(blocks)), NT * SG, 0, st>>>(coef, d, out, acc, L);
+}
+
+template <typename T>
+static void adi_strided(T lam, const T *d, T *out, int acc, const Lines &L, cudaStream_t st) {
+    switch (pow2_at_least((L.n + ADI_M - 1) / ADI_M)) {
+        case 1: launch_adi_strided<T, 1>(lam, d, out, acc, L, st); break;
+        case 2: launch_adi_strided<T, 2>(lam, d, out, acc, L, st); break;
+        case 4: launch_adi_strided<T, 4>(lam, d, out, acc, L, st); break;
+        case 8: launch_adi_strided<T, 8>(lam, d, out, acc, L, st); break;
+        case 16: launch_adi_strided<T, 16>(lam, d, out, acc, L, st); break;
+        default: launch_adi_strided<T, 32>(lam, d, out, acc, L, st); break;
+    }
+}
+
+template <typename T>
+static trid_status adi_run(T *u, const int64_t *n3, int ndim, T lam, int nsteps, T *w,
+                           cudaStream_t st) {
+    const int vec = is_aligned16(u) && is_aligned16(w) && (n3[0] * int64_t(sizeof(T))) % 16 == 0;
+    const int G = pow2_at_least((n3[0] + ADI_M - 1) / ADI_M);
+    Lines Ly{n3[0] * n3[2], n3[1], n3[0], n3[0]};
+    Lines Lz{n3[0] * n3[1], n3[2], n3[0] * n3[1], n3[0] * n3[1]};
+    for (int step = 0; step < nsteps; ++step) {
+        switch (G) {
+            case 1: launch_x_rhs<T, 1>(u, w, n3, ndim, lam, vec, st); break;
+            case 2: launch_x_rhs<T, 2>(u, w, n3, ndim, lam, vec, st); break;
+            case 4: launch_x_rhs<T, 4>(u, w, n3, ndim, lam, vec, st); break;
+            case 8: launch_x_rhs<T, 8>(u, w, n3, ndim, lam, vec, st); break;
+            case 16: launch_x_rhs<T, 16>(u, w, n3, ndim, lam, vec, st); break;
+            default: launch_x_rhs<T, 32>(u, w, n3, ndim, lam, vec, st); break;
+        }
+        if (ndim == 3) {
+            adi_strided<T>(lam, w, w, 0, Ly, st);
+            adi_strided<T>(lam, w, u, 1, Lz, st);
+        } else {
+            adi_strided<T>(lam, w, u, 1, Ly, st);
+        }
+        if (cudaGetLastError() != cudaSuccess) return TRID_ERR_CUDA;
+    }
+    return TRID_OK;
+}
+
+static trid_status adi_dims(const int64_t *dims, int ndim, int64_t (&n3)[3], int64_t &total) {
+    if (!dims || ndim < 2 || ndim > 3) return TRID_ERR_INVALID_ARG;
+    n3[0] = n3[1] = n3[2] = 1;
+    total = 1;
+    for (int k = 0; k < ndim; ++k) {
+        if (dims[k] < 3) return TRID_ERR_INVALID_ARG;
+        if (dims[k] > ADI_MAX_N) return TRID_ERR_UNSUPPORTED;
+        n3[k] = dims[k];
+        total *= dims[k];
+    }
+    return TRID_OK;
+}
+
+}  // namespace trid
+
+using namespace trid;
+
+extern "C" size_t adi_workspace_bytes(const int64_t *dims, int ndim, trid_dtype dtype) {
+    int64_t n3[3], total;
+    if (dtype != TRID_F32 && dtype != TRID_F64) return 0;
+    if (adi_dims(dims, ndim, n3, total) != TRID_OK) return 0;
+    const size_t esz = dtype == TRID_F32 ? 4 : 8;
+    return (size_t(total) * esz + 255) / 256 * 256;
+}
+
+extern "C" trid_status adi_step(void *u, const int64_t *dims, int ndim, double lambda,
+                                int nsteps, trid_dtype dtype, void *workspace,
+                                size_t workspace_bytes, trid_stream_t stream) {
+    int64_t n3[3], total;
+    if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
+    trid_status s = adi_dims(dims, ndim, n3, total);
+    if (s != TRID_OK) return s;
+    if (!u || nsteps < 0 || !(lambda > 0.0) || lambda > 1e30) return TRID_ERR_INVALID_ARG;
+    const size_t esz = dtype == TRID_F32 ? 4 : 8;
+    if ((reinterpret_cast<uintptr_t>(u) % esz) != 0) return TRID_ERR_MISALIGNED;
+    if (!workspace || workspace_bytes < adi_workspace_bytes(dims, ndim, dtype))
+        return TRID_ERR_ALLOC;
+    if ((reinterpret_cast<uintptr_t>(workspace) % 256) != 0) return TRID_ERR_MISALIGNED;
+    {
+        const char *pu = static_cast<const char *>(u), *pw = static_cast<const char *>(workspace);
+        const size_t bytes = size_t(total) * esz;
+        if (pu < pw + bytes && pw < pu + bytes) return TRID_ERR_INVALID_ARG;
+    }
+    if (nsteps == 0) return TRID_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (dtype == TRID_F32)
+        return adi_run<float>(static_cast<float *>(u), n3, ndim, float(lambda), nsteps,
+                              static_cast<float *>(workspace), st);
+    return adi_run<double>(static_cast<double *>(u), n3, ndim, lambda, nsteps,
+                           static_cast<double *>(workspace), st);
+}

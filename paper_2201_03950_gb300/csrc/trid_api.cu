@@ -1,0 +1,92 @@
+// trid_api.cu -- status strings, version, device status word and the
+// library-owned scratch pool behind trid_solve_batch.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "trid_internal.h"
+
+namespace trid {
+
+__device__ int g_status_word;  // 0 = OK, else a trid_status recorded by a kernel
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+void *g_pool_ptr[kMaxDevices] = {};
+size_t g_pool_size[kMaxDevices] = {};
+int *g_status_ptr[kMaxDevices] = {};
+}  // namespace
+
+trid_status pool_reserve(size_t bytes, void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TRID_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_size[dev] < bytes) {
+        if (g_pool_ptr[dev]) {
+            // in-flight work may still use the old buffer
+            if (cudaDeviceSynchronize() != cudaSuccess) return TRID_ERR_CUDA;
+            cudaFree(g_pool_ptr[dev]);
+            g_pool_ptr[dev] = nullptr;
+            g_pool_size[dev] = 0;
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return TRID_ERR_ALLOC;
+        }
+        g_pool_ptr[dev] = p;
+        g_pool_size[dev] = bytes;
+    }
+    *out = g_pool_ptr[dev];
+    return TRID_OK;
+}
+
+int *device_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_status_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_status_ptr[dev] = static_cast<int *>(p);
+    }
+    return g_status_ptr[dev];
+}
+
+}  // namespace trid
+
+extern "C" const char *trid_status_string(trid_status s) {
+    switch (s) {
+        case TRID_OK: return "TRID_OK";
+        case TRID_ERR_INVALID_ARG: return "TRID_ERR_INVALID_ARG";
+        case TRID_ERR_UNSUPPORTED: return "TRID_ERR_UNSUPPORTED";
+        case TRID_ERR_MISALIGNED: return "TRID_ERR_MISALIGNED";
+        case TRID_ERR_CUDA: return "TRID_ERR_CUDA";
+        case TRID_ERR_ALLOC: return "TRID_ERR_ALLOC";
+        case TRID_ERR_TIMEOUT: return "TRID_ERR_TIMEOUT";
+    }
+    return "TRID_ERR_UNKNOWN";
+}
+
+extern "C" const char *trid_version(void) { return "gb300-trid 0.1 (sm_103a)"; }
+
+extern "C" trid_status trid_get_device_status(trid_stream_t stream) {
+    int *w = trid::device_status_word();
+    if (!w) return TRID_ERR_CUDA;
+    int h = 0;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return TRID_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return TRID_ERR_CUDA;
+    if (h != 0) {
+        const int zero = 0;
+        if (cudaMemcpyAsync(w, &zero, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return TRID_ERR_CUDA;
+    }
+    return static_cast<trid_status>(h);
+}

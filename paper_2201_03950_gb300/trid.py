@@ -1,0 +1,164 @@
+"""Thin ctypes binding of the C ABI in ``include/trid.h`` (libtrid.so).
+
+Argument marshalling only: device pointers come from torch CUDA tensors
+(``tensor.data_ptr()``), the stream from ``torch.cuda.current_stream()``, and
+every step of the computation runs in the library's CUDA kernels.  There is no
+CPU fallback: if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+TRID_F32, TRID_F64 = 0, 1
+STATUS = {0: "TRID_OK", 1: "TRID_ERR_INVALID_ARG", 2: "TRID_ERR_UNSUPPORTED",
+          3: "TRID_ERR_MISALIGNED", 4: "TRID_ERR_CUDA", 5: "TRID_ERR_ALLOC",
+          6: "TRID_ERR_TIMEOUT"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TridError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libtrid.so (built in-tree by ``build.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None or path is not None:
+            p = path or _build.LIB
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library {p} is missing: run build() first "
+                                   "(there is no CPU fallback)")
+            L = ctypes.CDLL(p)
+            _bind(L)
+            if path is not None:
+                return L
+            _lib = L
+    return _lib
+
+
+def _bind(L):
+    P, i32, i64, f64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    sigs = {
+        "trid_solve_batch": ([P, P, P, P, P, P, i32, i32, i32, P], i32),
+        "trid_solve_batch_ws": ([P, P, P, P, P, P, i32, i32, i32, P, sz, P], i32),
+        "trid_solve_workspace_bytes": ([P, i32, i32, i32], sz),
+        "adi_step": ([P, P, i32, f64, i32, i32, P, sz, P], i32),
+        "adi_workspace_bytes": ([P, i32, i32], sz),
+        "trid_get_device_status": ([P], i32),
+        "trid_status_string": ([i32], ctypes.c_char_p),
+        "trid_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+def _dims(dims):
+    n = len(dims)
+    return (ctypes.c_int64 * max(n, 1))(*[int(v) for v in dims]), n
+
+
+def _dtype(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return TRID_F32
+    if t.dtype == torch.float64:
+        return TRID_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensors(ts, dtype_ref, numel):
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensors must be CUDA tensors")
+        if t.dtype != dtype_ref.dtype:
+            raise TypeError("all arrays must share one dtype")
+        if not t.is_contiguous() or t.numel() != numel:
+            raise ValueError(f"arrays must be contiguous with {numel} elements")
+
+
+def solve(a, b, c, d, dims, solve_dim: int, u=None, workspace=None, stream=None):
+    """Batched solve along ``solve_dim`` of a column-major mesh ``dims``
+    (dims[0] contiguous).  u is None: x overwrites d.  Otherwise u += x."""
+    numel = 1
+    for v in dims:
+        numel *= int(v)
+    _check_tensors((a, b, c, d, u), d, numel)
+    L = load()
+    dc, nd = _dims(dims)
+    if workspace is None:
+        st = L.trid_solve_batch(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(u), dc, nd, solve_dim,
+                                _dtype(d), _stream(stream))
+    else:
+        st = L.trid_solve_batch_ws(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(u), dc, nd,
+                                   solve_dim, _dtype(d), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream))
+    if st != 0:
+        raise TridError(st, "trid_solve_batch")
+    return u if u is not None else d
+
+
+def solve_workspace_bytes(dims, solve_dim: int, dtype) -> int:
+    dc, nd = _dims(dims)
+    code = TRID_F32 if str(dtype).endswith("float32") else TRID_F64
+    return int(load().trid_solve_workspace_bytes(dc, nd, solve_dim, code))
+
+
+def adi_workspace_bytes(dims, dtype) -> int:
+    dc, nd = _dims(dims)
+    code = TRID_F32 if str(dtype).endswith("float32") else TRID_F64
+    return int(load().adi_workspace_bytes(dc, nd, code))
+
+
+def adi_step(u, dims, lam: float, nsteps: int, workspace, stream=None):
+    """Advance u in place by ``nsteps`` ADI steps (Dirichlet-zero boundary)."""
+    numel = 1
+    for v in dims:
+        numel *= int(v)
+    _check_tensors((u,), u, numel)
+    L = load()
+    dc, nd = _dims(dims)
+    st = L.adi_step(_ptr(u), dc, nd, float(lam), int(nsteps), _dtype(u), _ptr(workspace),
+                    workspace.numel() * workspace.element_size(), _stream(stream))
+    if st != 0:
+        raise TridError(st, "adi_step")
+    return u
+
+
+def device_status(stream=None) -> int:
+    return int(load().trid_get_device_status(_stream(stream)))
+
+
+def status_string(code: int) -> str:
+    return load().trid_status_string(int(code)).decode()
+
+
+def version() -> str:
+    return load().trid_version().decode()
