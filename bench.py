@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: batched tridiagonal solves along x, y and z of a
+256^3 FP32 mesh plus one 3D ADI heat-diffusion step (lambda = 0.1).
+
+One step = solve(x) + solve(y) + solve(z) + adi_step(1 step), each call timed
+with CUDA events on the launching stream, with d restored from a pristine copy
+and L2 flushed (a 256 MiB write) before every call, outside the events.
+
+Metric: algorithmic bandwidth of the step in GB/s, counting 5 words per
+unknown for a solve (a, b, c, d read; x written -- the paper's convention,
+Table 1) and 5 words per mesh point for the ADI step (two-pass minimum: u read,
+intermediate written; intermediate and u read, u written).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on the host cores on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (the solves
+shard with no exchange); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (256, 256, 256)
+LAM = 0.1
+METRIC = "Batched tridiag solve GB/s (% HBM roofline), 256³ FP32 x/y/z; ADI step ms"
+WORKLOAD = "256^3 FP32: batched solves along x, y, z (65536 systems of 256 each) + one 3D ADI step"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--dtype", choices=["f32", "f64"], default="f32",
+                   help="f64 runs the same step in FP64 (reported separately; the headline is f32)")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel sources changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2201_03950_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    digest = h.hexdigest()[:16]
+    for line in open(path):
+        m = re.match(r"\|\s*(\S+)\s*\|\s*([0-9.]+)\s*\|\s*([0-9a-f]{16})\s*\|", line)
+        if m and m.group(1) == kernel_key:
+            return float(m.group(2)) if m.group(3) == digest else None
+    return None
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = [r.split(",") for r in open(self.tmp.name).read().strip().splitlines()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_2201_03950_gb300 import build, inputs, metrics, trid
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    trid.load()
+
+    total = int(np.prod(DIMS))
+    npdt = np.float32 if args.dtype == "f32" else np.float64
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    esz = np.dtype(npdt).itemsize
+    a, b, c, d = inputs.dominant_system((total,), seed=rank, dtype=npdt)
+    modes = inputs.sine_modes(DIMS, seed=rank)
+    u0 = inputs.sine_field(DIMS, modes, dtype=npdt)
+    ta, tb, tc, td0 = (torch.from_numpy(v).to(dev) for v in (a, b, c, d))
+    td = torch.empty_like(td0)
+    tu = torch.from_numpy(u0).to(dev)
+    ws = torch.empty(trid.adi_workspace_bytes(DIMS, tdt), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    names = ["solve_x", "solve_y", "solve_z", "adi_step"]
+    launches_per_step = 3 * 1 + 3  # one kernel per solve; RHS+x, y, z+accumulate per ADI step
+    nbytes = {"solve_x": metrics.solve_bytes(total, esz), "solve_y": metrics.solve_bytes(total, esz),
+              "solve_z": metrics.solve_bytes(total, esz),
+              "adi_step": metrics.adi_step_bytes(total, esz)}
+
+    def one_step(record):
+        evs = []
+        for k in range(3):
+            td.copy_(td0)
+            flush.fill_(k + 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            trid.solve(ta, tb, tc, td, DIMS, k, stream=stream)
+            e1.record(stream)
+            evs.append((names[k], e0, e1))
+        flush.fill_(7)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        trid.adi_step(tu, DIMS, LAM, 1, ws, stream=stream)
+        e1.record(stream)
+        evs.append(("adi_step", e0, e1))
+        if record is not None:
+            record.append(evs)
+
+    for _ in range(args.warmup):
+        one_step(None)
+    clocks = Clocks(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    recs = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        one_step(recs)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clock_info = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    per = {n: [] for n in names}
+    for evs in recs:
+        for n, e0, e1 in evs:
+            per[n].append(e0.elapsed_time(e1))
+    ms_step = sum(sum(v) for v in per.values()) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    step_bytes = sum(nbytes.values())
+    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+
+    # ---- end to end through the public API with pinned host buffers
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in
+            (("a", a), ("b", b), ("c", c), ("d", d), ("u", u0))}
+    host_x = torch.empty(total, dtype=tdt).pin_memory()
+    e2e_ms = []
+    h2d = 3 * 4 * total * esz + total * esz
+    d2h = 3 * total * esz + total * esz
+    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(3):
+            ta.copy_(host["a"], non_blocking=True)
+            tb.copy_(host["b"], non_blocking=True)
+            tc.copy_(host["c"], non_blocking=True)
+            td.copy_(host["d"], non_blocking=True)
+            trid.solve(ta, tb, tc, td, DIMS, k, stream=stream)
+            host_x.copy_(td, non_blocking=True)
+        tu.copy_(host["u"], non_blocking=True)
+        trid.adi_step(tu, DIMS, LAM, 1, ws, stream=stream)
+        host_x.copy_(tu, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_step_ms = statistics.median(e2e_ms) if e2e_ms else None
+    e2e_val = world * step_bytes / (e2e_step_ms * 1e-3) / 1e9 if e2e_ms else None
+
+    peak, peak_kind = peaks()
+    means = {n: statistics.mean(v) for n, v in per.items()}
+    solve_frac = {n: {"us": round(means[n] * 1e3, 2),
+                      "GBps": round(nbytes[n] / (means[n] * 1e-3) / 1e9, 1),
+                      "frac": round(nbytes[n] / (means[n] * 1e-3) / 1e9 / peak, 4)}
+                  for n in names}
+    dom = max(["solve_x", "solve_y", "solve_z"], key=lambda n: means[n])
+    achieved = nbytes[dom] / (means[dom] * 1e-3) / 1e9
+    traffic = profiled_traffic(f"{dom}_{args.dtype}_256")
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+        "data": "synthetic (seeded diagonally dominant coefficients; ADI from 3 sine eigenmodes)",
+        "config": {"workload": WORKLOAD, "dims": list(DIMS), "lambda": LAM,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "flushed before every timed call (256 MiB write); inputs 256 MiB per solve",
+                   "timing": "CUDA events per call on the launching stream, summed per step"},
+        "per_call": solve_frac,
+        "adi_step_ms": round(means["adi_step"], 4),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": f"{peak_kind} (copy, burst)", "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_launch": nbytes[dom]},
+        "e2e": None if e2e_val is None else {
+            "value": round(e2e_val, 2), "unit": "GB/s", "ms_per_step": round(e2e_step_ms, 3),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clock_info,
+        "wall_s_timed_region": round(t_wall, 3),
+    }
+    if args.dtype != "f32":
+        out["metric"] = METRIC + " [FP64 variant of the step]"
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_sample(target_s=10.0)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------- oracle (CPU) side
+def oracle_step(arrs, dims_s, u_adi, dims_adi):
+    """One step of the oracle on (possibly sub-sampled) meshes; returns
+    (seconds, algorithmic bytes in the FP32 convention)."""
+    import oracle
+    a, b, c, d = arrs
+    t0 = time.perf_counter()
+    nb = 0
+    for k in range(3):
+        oracle.solve_mesh(a, b, c, d, dims_s[k], k)
+        nb += 5 * int(np.prod(dims_s[k])) * 4
+    oracle.adi(u_adi, dims_adi, LAM, 1)
+    nb += 5 * int(np.prod(dims_adi)) * 4
+    return time.perf_counter() - t0, nb
+
+
+def sample_meshes(frac: float):
+    """Sub-meshes holding ~frac of the systems of each solve: the outermost
+    axis that is not the solve axis is shortened, system lengths stay 256.
+    The ADI sample keeps full x/y planes and ~frac of the z planes."""
+    n = DIMS[0]
+    m = max(3, int(round(n * frac)))
+    dims_s = [(n, n, m), (n, n, m), (n, m, n)]
+    return dims_s, (n, n, max(3, m))
+
+
+def cpu_baseline_sample(target_s: float = 10.0):
+    import oracle
+    from paper_2201_03950_gb300 import inputs
+    dims_s, dims_adi = sample_meshes(1.0)
+    total = int(np.prod(DIMS))
+    arrs = [v.astype(np.float64) for v in inputs.dominant_system((total,), seed=0, dtype=np.float32)]
+    u = inputs.sine_field(dims_adi, inputs.sine_modes(dims_adi, seed=0), dtype=np.float32)
+    u = u.astype(np.float64)
+    oracle.load()
+    secs, nbytes, reps = 0.0, 0, 0
+    while secs < target_s and reps < 10:
+        s, nb = oracle_step(arrs, dims_s, u, dims_adi)
+        secs += s
+        nbytes += nb
+        reps += 1
+    return {"value": round(nbytes / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full step(s): FP64 oracle solves along x, y, z of 256^3 + one 256^3 "
+                      f"ADI step, single-threaded C ({secs:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2201_03950_gb300 import inputs
+    oracle.load()
+    # size each step so that the whole run stays within ~2 minutes
+    full_step_s = 3.5
+    frac = min(1.0, 120.0 / max(1, args.steps + args.warmup) / full_step_s)
+    dims_s, dims_adi = sample_meshes(frac)
+    total = int(np.prod(DIMS))
+    arrs = [v.astype(np.float64) for v in inputs.dominant_system((total,), seed=0, dtype=np.float32)]
+    u = inputs.sine_field(dims_adi, inputs.sine_modes(dims_adi, seed=0)).astype(np.float64)
+    for _ in range(args.warmup):
+        oracle_step(arrs, dims_s, u, dims_adi)
+    secs, nbytes = 0.0, 0
+    for _ in range(args.steps):
+        s, nb = oracle_step(arrs, dims_s, u, dims_adi)
+        secs += s
+        nbytes += nb
+    val = nbytes / secs / 1e9
+    sample = (f"per step: FP64 oracle solves on sub-meshes {dims_s} (systems of 256) + one ADI "
+              f"step on {dims_adi}, single-threaded C; {frac:.3f} of the 256^3 workload")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(secs / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (bounded CPU sample)", "dims": list(DIMS)},
+        "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

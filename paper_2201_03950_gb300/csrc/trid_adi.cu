@@ -136,10 +136,13 @@ static void launch_adi_strided(T lam, const T *d, T *out, int acc, const Lines &
                                cudaStream_t st) {
     // at least one full warp per block: the reduced solve shuffles over all 32 lanes
     constexpr int SG = (NT * SysCfg<T>::SG < 32) ? 32 / NT : SysCfg<T>::SG;
-    const int64_t blocks = (L.nsys + SG - 1) / SG;
     AdiCoef<T> coef{lam};
-    k_strided<T, ADI_M, NT, SG, AdiCoef<T>>
-        <<<dim3(unsigned(blocks)), NT * SG, 0, st>>>(coef, d, out, acc, L);
+    if (acc)
+        k_strided<T, ADI_M, NT, SG, true, AdiCoef<T>>
+            <<<strided_grid(L, SG), NT * SG, 0, st>>>(coef, d, out, L, L.nsys / L.inner);
+    else
+        k_strided<T, ADI_M, NT, SG, false, AdiCoef<T>>
+            <<<strided_grid(L, SG), NT * SG, 0, st>>>(coef, d, out, L, L.nsys / L.inner);
 }
 
 template <typename T>

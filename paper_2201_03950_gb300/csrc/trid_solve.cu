@@ -254,10 +254,13 @@ static void launch_strided(const T *a, const T *b, const T *c, const T *d, T *ou
                            const Lines &L, cudaStream_t st) {
     // at least one full warp per block: the reduced solve shuffles over all 32 lanes
     constexpr int SG = (NT * SysCfg<T>::SG < 32) ? 32 / NT : SysCfg<T>::SG;
-    const int64_t blocks = (L.nsys + SG - 1) / SG;
     ArrayCoef<T> coef{a, b, c};
-    k_strided<T, TILE_M, NT, SG, ArrayCoef<T>>
-        <<<dim3(unsigned(blocks)), NT * SG, 0, st>>>(coef, d, out, acc, L);
+    if (acc)
+        k_strided<T, TILE_M, NT, SG, true, ArrayCoef<T>>
+            <<<strided_grid(L, SG), NT * SG, 0, st>>>(coef, d, out, L, L.nsys / L.inner);
+    else
+        k_strided<T, TILE_M, NT, SG, false, ArrayCoef<T>>
+            <<<strided_grid(L, SG), NT * SG, 0, st>>>(coef, d, out, L, L.nsys / L.inner);
 }
 
 template <typename T>
@@ -280,6 +283,7 @@ static trid_status solve_lines(const T *a, const T *b, const T *c, const T *d, T
                 default: launch_lines<T, 32>(a, b, c, d, out, acc, L, vec_ok, st); break;
             }
         } else {
+            if (!strided_offsets_fit(L)) return TRID_ERR_UNSUPPORTED;
             switch (G) {
                 case 1: launch_strided<T, 1>(a, b, c, d, out, acc, L, st); break;
                 case 2: launch_strided<T, 2>(a, b, c, d, out, acc, L, st); break;
