@@ -16,6 +16,8 @@
 #include "../../include/trid.h"
 #include "trid_internal.h"
 
+#include <type_traits>
+
 namespace trid {
 
 constexpr int ADI_M = 8;
@@ -38,16 +40,14 @@ template <typename T, int M, int G>
 __global__ void __launch_bounds__(256)
 k_adi_x_rhs(const T *__restrict__ u, T *__restrict__ w, int64_t nx, int64_t ny, int64_t nz,
             int ndim, T lam, int vec_ok) {
+    // grid: x over groups of lines of one plane, y over planes (no division)
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int g = lane % G;
-    const int64_t line = warp * (32 / G) + lane / G;
-    const int64_t nlines = ny * nz;
-    const bool active = line < nlines;
-    const int64_t y = active ? line % ny : 0;
-    const int64_t z = active ? line / ny : 0;
+    const int y = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / G) + lane / G;
+    const int z = int(blockIdx.y);
+    const bool active = y < ny;
     const bool interior = active && y > 0 && y < ny - 1 && (ndim == 2 || (z > 0 && z < nz - 1));
-    const int64_t base = line * nx;
+    const int64_t base = (int64_t(z) * ny + y) * nx;
     const int64_t i0 = int64_t(g) * M;
     const bool vec = vec_ok != 0;
 
@@ -124,11 +124,10 @@ static int pow2_at_least(int64_t v) {
 template <typename T, int G>
 static void launch_x_rhs(const T *u, T *w, const int64_t *n3, int ndim, T lam, int vec,
                          cudaStream_t st) {
-    const int64_t lines = n3[1] * n3[2];
-    const int64_t warps = (lines + (32 / G) - 1) / (32 / G);
+    const int64_t warps = (n3[1] + (32 / G) - 1) / (32 / G);  // per plane
     const int64_t blocks = (warps + 7) / 8;
-    k_adi_x_rhs<T, ADI_M, G><<<dim3(unsigned(blocks)), 256, 0, st>>>(u, w, n3[0], n3[1], n3[2],
-                                                                      ndim, lam, vec);
+    k_adi_x_rhs<T, ADI_M, G><<<dim3(unsigned(blocks), unsigned(n3[2])), 256, 0, st>>>(
+        u, w, n3[0], n3[1], n3[2], ndim, lam, vec);
 }
 
 template <typename T, int NT>
@@ -137,6 +136,12 @@ static void launch_adi_strided(T lam, const T *d, T *out, int acc, const Lines &
     // at least one full warp per block: the reduced solve shuffles over all 32 lanes
     constexpr int SG = (NT * SysCfg<T>::SG < 32) ? 32 / NT : SysCfg<T>::SG;
     AdiCoef<T> coef{lam};
+    if constexpr (std::is_same<T, float>::value) {
+        const void *arrs[2] = {d, out};
+        const bool ok = acc ? launch_strided_tma<T, ADI_M, NT, 16, true>(arrs, coef, out, L, st)
+                            : launch_strided_tma<T, ADI_M, NT, 16, false>(arrs, coef, out, L, st);
+        if (ok) return;
+    }
     if (acc)
         k_strided<T, ADI_M, NT, SG, true, AdiCoef<T>>
             <<<strided_grid(L, SG), NT * SG, 0, st>>>(coef, d, out, L, L.nsys / L.inner);

@@ -1,6 +1,8 @@
 // trid_api.cu -- status strings, version, device status word and the
 // library-owned scratch pool behind trid_solve_batch.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <mutex>
 
@@ -16,7 +18,65 @@ std::mutex g_pool_mu;
 void *g_pool_ptr[kMaxDevices] = {};
 size_t g_pool_size[kMaxDevices] = {};
 int *g_status_ptr[kMaxDevices] = {};
+DeviceInfo g_info[kMaxDevices];
+bool g_info_ok[kMaxDevices] = {};
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+bool g_encode_tried = false;
 }  // namespace
+
+const DeviceInfo *device_info() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_info_ok[dev]) {
+        DeviceInfo d{};
+        if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_info[dev] = d;
+        g_info_ok[dev] = true;
+    }
+    return &g_info[dev];
+}
+
+bool encode_lines_map(void *map, const void *base, int esz, int64_t inner, int64_t n,
+                      int64_t outer, int box_x) {
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_encode_tried) {
+            g_encode_tried = true;
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                 cudaEnableDefault, &q) == cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+            else
+                cudaGetLastError();
+        }
+    }
+    if (!g_encode) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+    if ((inner * esz) % 16 != 0 || n < 1 || n > 256 || inner < 1 || outer < 1) return false;
+    if (inner >= (int64_t(1) << 32) || outer >= (int64_t(1) << 31)) return false;
+    const cuuint64_t dims[3] = {cuuint64_t(inner), cuuint64_t(n), cuuint64_t(outer)};
+    const cuuint64_t strides[2] = {cuuint64_t(inner * esz), cuuint64_t(inner * n * esz)};
+    if (strides[1] >= (cuuint64_t(1) << 40)) return false;
+    const cuuint32_t box[3] = {cuuint32_t(box_x), cuuint32_t(n), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = g_encode(
+        static_cast<CUtensorMap *>(map),
+        esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+        const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 trid_status pool_reserve(size_t bytes, void **out) {
     int dev = 0;

@@ -15,6 +15,19 @@ inline bool is_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p)
 // too small.  Shared by all calls on that device.
 trid_status pool_reserve(size_t bytes, void **out);
 
+// Cached attributes of the current device (queried on first use per device).
+struct DeviceInfo {
+    int sm_count;
+    int max_smem_optin;   // dynamic shared memory a block may opt in to
+    int smem_per_sm;
+};
+const DeviceInfo *device_info();
+
+// 3D tensor map over a strided line set viewed as (inner, n, outer) with the
+// box (box_x, n, 1); false if the TMA constraints do not hold.
+bool encode_lines_map(void *map /* CUtensorMap */, const void *base, int esz, int64_t inner,
+                      int64_t n, int64_t outer, int box_x);
+
 // Device address of the status word of the current device (see
 // trid_get_device_status); kernels that run bounded waits record failures there.
 int *device_status_word();

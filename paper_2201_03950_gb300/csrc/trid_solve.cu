@@ -26,6 +26,7 @@
 #include "trid_internal.h"
 
 #include <cstdio>
+#include <type_traits>
 
 namespace trid {
 
@@ -255,6 +256,15 @@ static void launch_strided(const T *a, const T *b, const T *c, const T *d, T *ou
     // at least one full warp per block: the reduced solve shuffles over all 32 lanes
     constexpr int SG = (NT * SysCfg<T>::SG < 32) ? 32 / NT : SysCfg<T>::SG;
     ArrayCoef<T> coef{a, b, c};
+    if constexpr (std::is_same<T, float>::value) {
+      if (b != nullptr) {
+        // Blackwell path: TMA-staged tiles (16 systems x n rows per box)
+        const void *arrs[5] = {a, b, c, d, out};
+        const bool ok = acc ? launch_strided_tma<T, TILE_M, NT, 16, true>(arrs, coef, out, L, st)
+                            : launch_strided_tma<T, TILE_M, NT, 16, false>(arrs, coef, out, L, st);
+        if (ok) return;
+      }
+    }
     if (acc)
         k_strided<T, TILE_M, NT, SG, true, ArrayCoef<T>>
             <<<strided_grid(L, SG), NT * SG, 0, st>>>(coef, d, out, L, L.nsys / L.inner);

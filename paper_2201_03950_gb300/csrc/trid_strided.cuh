@@ -11,6 +11,8 @@
 // come back the same way.
 #pragma once
 #include "trid_device.cuh"
+#include "trid_tma.cuh"
+#include "trid_internal.h"
 
 namespace trid {
 
@@ -37,6 +39,14 @@ struct ArrayCoef {
         rb = b ? b[off] : T(1);
         rc = (i == n - 1) ? T(0) : c[off];
     }
+    // TMA path: a, b, c staged in shared memory slots 0..2
+    static constexpr int NCOEF = 3;
+    __device__ __forceinline__ void get_smem(const T *sa, const T *sb, const T *sc, int k, int i,
+                                             int n, T &ra, T &rb, T &rc) const {
+        ra = (i == 0) ? T(0) : sa[k];
+        rb = sb[k];
+        rc = (i == n - 1) ? T(0) : sc[k];
+    }
 };
 
 // The ADI operator of Section 4.1 generated in the kernel:
@@ -51,6 +61,11 @@ struct AdiCoef {
         ra = bnd ? T(0) : -lam;
         rb = bnd ? T(1) : T(1) + T(2) * lam;
         rc = bnd ? T(0) : -lam;
+    }
+    static constexpr int NCOEF = 0;
+    __device__ __forceinline__ void get_smem(const T *, const T *, const T *, int, int i, int n,
+                                             T &ra, T &rb, T &rc) const {
+        get(0, i, n, ra, rb, rc);
     }
 };
 
@@ -137,6 +152,147 @@ k_strided(Coef coef, const T *d, T *out, Lines L, int64_t outer) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA-fed variant (Blackwell): one producer warp streams boxes of
+// [SG systems x n rows] of every input array through a ring of `stages`
+// shared-memory buffers (3D tensor map over (inner, n, outer), box
+// (SG, n, 1)); NT*SG consumer threads take their tile rows from shared memory
+// and solve exactly as k_strided.  The loads of the next batches are in flight
+// while the current batch is solved, and the consumers issue no global loads.
+// Persistent: the grid walks the batches (x-chunk, outer index).
+// Shared memory: stages x slots x [n][SG] staging, 8 reduced tables, mbarriers.
+// ---------------------------------------------------------------------------
+template <typename T, int NT, int SG>
+struct TmaLayout {
+    static constexpr int P = SG + 1;
+    __host__ __device__ static size_t slot_bytes(int n) { return (size_t(n) * SG * sizeof(T) + 127) / 128 * 128; }
+    __host__ __device__ static size_t table_bytes() { return (8 * NT * P * sizeof(T) + 127) / 128 * 128; }
+    __host__ __device__ static size_t bytes(int n, int nslots, int stages) {
+        return size_t(stages) * nslots * slot_bytes(n) + table_bytes() + 2 * 8 * size_t(stages);
+    }
+};
+
+template <typename T, int M, int NT, int SG, bool ACC, typename Coef>
+__global__ void __launch_bounds__(NT * SG + 32, 2)
+k_strided_tma(const __grid_constant__ TmaSet maps, Coef coef, T *out, Lines L, int64_t nbatch,
+              int stages, int *status) {
+    using LY = TmaLayout<T, NT, SG>;
+    constexpr int P = LY::P;
+    constexpr int NCONS = NT * SG;
+    static_assert(NCONS % 32 == 0, "consumers must be whole warps");
+    constexpr int NSLOT = Coef::NCOEF + 1 + (ACC ? 1 : 0);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int n = int(L.n);
+    const size_t slot_bytes = LY::slot_bytes(n);
+    const size_t stage_bytes = NSLOT * slot_bytes;
+    T *tab = reinterpret_cast<T *>(smem + stages * stage_bytes);
+    T *s_as = tab, *s_cs = tab + NT * P, *s_ds = tab + 2 * NT * P;
+    T *s_ae = tab + 3 * NT * P, *s_ce = tab + 4 * NT * P, *s_de = tab + 5 * NT * P;
+    T *s_xs = tab + 6 * NT * P, *s_xe = tab + 7 * NT * P;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + stages * stage_bytes + LY::table_bytes());
+    uint64_t *empty = full + stages;
+
+    __shared__ int abort_flag;  // set once a bounded wait gave up: later waits are skipped
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCONS / 32);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int64_t nxc = (L.inner + SG - 1) / SG;
+
+    if (tid >= NCONS) {
+        // producer warp: one elected lane issues the copies
+        if (tid == NCONS) {
+            const uint32_t tx = uint32_t(NSLOT) * uint32_t(n) * SG * sizeof(T);
+            int k = 0;
+            for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x, ++k) {
+                const int s = k % stages;
+                if (k >= stages && !mbar_wait(&empty[s], uint32_t((k / stages) - 1) & 1u, status)) {
+                    *(volatile int *)&abort_flag = 1;
+                    break;
+                }
+                mbar_expect_tx(&full[s], tx);
+                const int x0 = int((bt % nxc) * SG);
+                const int o = int(bt / nxc);
+                unsigned char *dst = smem + s * stage_bytes;
+#pragma unroll
+                for (int q = 0; q < NSLOT; ++q)
+                    tma_load_3d(dst + q * slot_bytes, &maps.map[q], x0, 0, o, &full[s]);
+            }
+        }
+        return;
+    }
+
+    const int lane = tid & 31;
+    const int sl = tid % SG;
+    const int tile = tid / SG;
+    const int i0 = tile * M;
+    const bool full_tile = (i0 + M <= n);
+    const int w = tile * P + sl;
+    const int stride = int(L.stride);
+    int k = 0;
+    for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x, ++k) {
+        const int s = k % stages;
+        bool ok = false;
+        if (!*(volatile int *)&abort_flag) {
+            ok = mbar_wait(&full[s], uint32_t(k / stages) & 1u, status);
+            if (!ok) *(volatile int *)&abort_flag = 1;
+        }
+        const unsigned char *stg = smem + s * stage_bytes;
+        const T *sa = reinterpret_cast<const T *>(stg);
+        const T *sb = reinterpret_cast<const T *>(stg + slot_bytes);
+        const T *sc = reinterpret_cast<const T *>(stg + 2 * slot_bytes);
+        const T *sd = reinterpret_cast<const T *>(stg + Coef::NCOEF * slot_bytes);
+        const T *su = reinterpret_cast<const T *>(stg + (Coef::NCOEF + 1) * slot_bytes);
+        const int64_t x = (bt % nxc) * SG + sl;
+        const int64_t o = bt / nxc;
+        const bool active = ok && x < L.inner;
+        T ra[M], rb[M], rc[M], rd[M], ru[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const int i = i0 + j;
+            if (active && (full_tile || i < n)) {
+                const int q = i * SG + sl;
+                coef.get_smem(sa, sb, sc, q, i, n, ra[j], rb[j], rc[j]);
+                rd[j] = sd[q];
+                if (ACC) ru[j] = su[q];
+            } else {
+                ra[j] = T(0); rb[j] = T(1); rc[j] = T(0); rd[j] = T(0);
+                if (ACC) ru[j] = T(0);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+
+        T as, cs, ds, ae, ce, de;
+        tile_reduce<T, M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
+        s_as[w] = as; s_cs[w] = cs; s_ds[w] = ds;
+        s_ae[w] = ae; s_ce[w] = ce; s_de[w] = de;
+        named_barrier(1, NCONS);
+        {
+            const int rs = tid / NT, rt = tid % NT;
+            const int q = rt * P + rs;
+            T xs, xe;
+            group_solve<T, NT>(s_as[q], s_cs[q], s_ds[q], s_ae[q], s_ce[q], s_de[q], rt, xs, xe);
+            s_xs[q] = xs;
+            s_xe[q] = xe;
+        }
+        named_barrier(1, NCONS);
+        tile_substitute<T, M>(ra, rc, rd, s_xs[w], s_xe[w]);
+        if (active) {
+            T *ob = out + (x + o * L.inner * L.n);
+#pragma unroll
+            for (int j = 0; j < M; ++j)
+                if (full_tile || i0 + j < n) ob[(i0 + j) * stride] = ACC ? rd[j] + ru[j] : rd[j];
+        }
+    }
+}
 }  // namespace trid
 
 namespace trid {
@@ -153,4 +309,61 @@ inline dim3 strided_grid(const Lines &L, int SG) {
 inline bool strided_offsets_fit(const Lines &L) {
     return (L.n - 1) * L.stride < (int64_t(1) << 31) && L.n < (int64_t(1) << 31);
 }
+
+// Host launcher of k_strided_tma.  `arrs` = the Coef::NCOEF coefficient
+// arrays, then d, then (ACC) u.  Returns false, having launched nothing, when
+// the TMA constraints do not hold (the caller then uses k_strided).
+template <typename T, int M, int NT, int SG, bool ACC, typename Coef>
+inline bool launch_strided_tma(const void *const *arrs, Coef coef, T *out, const Lines &L,
+                               cudaStream_t st) {
+    // the consumer group must be whole warps (named barrier, per-warp arrivals)
+    if constexpr ((NT * SG) % 32 != 0 || NT * SG + 32 > 1024) {
+        return false;
+    } else {
+    constexpr int NSLOT = Coef::NCOEF + 1 + (ACC ? 1 : 0);
+    const DeviceInfo *di = device_info();
+    if (!di || L.n > NT * M || L.inner < 1) return false;
+    const int64_t outer = L.nsys / L.inner;
+    TmaSet maps;
+    for (int q = 0; q < NSLOT; ++q)
+        if (!encode_lines_map(&maps.map[q], arrs[q], int(sizeof(T)), L.inner, L.n, outer, SG))
+            return false;
+    using LY = TmaLayout<T, NT, SG>;
+    // Prefer two blocks per SM (two consumer groups hide each other's barrier
+    // and recurrence latency), each with as many stages (<= 4) as then fit.
+    const size_t per_block = size_t(di->smem_per_sm) / 2 - 1024;
+    const size_t cap = per_block < size_t(di->max_smem_optin) ? per_block
+                                                                : size_t(di->max_smem_optin);
+    int stages = 4;
+    while (stages > 1 && LY::bytes(int(L.n), NSLOT, stages) > cap) --stages;
+    if (LY::bytes(int(L.n), NSLOT, stages) > cap) {
+        // one block per SM: deepen the pipeline instead
+        stages = 4;
+        while (stages > 1 && LY::bytes(int(L.n), NSLOT, stages) > size_t(di->max_smem_optin))
+            --stages;
+    }
+    const size_t smem = LY::bytes(int(L.n), NSLOT, stages);
+    if (smem > size_t(di->max_smem_optin)) return false;
+    auto kern = k_strided_tma<T, M, NT, SG, ACC, Coef>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT * SG + 32, smem) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    const int64_t nbatch = (L.inner + SG - 1) / SG * outer;
+    const int64_t slots = int64_t(di->sm_count) * per_sm;
+    const int64_t grid = nbatch < slots ? nbatch : slots;
+    kern<<<dim3(unsigned(grid)), NT * SG + 32, smem, st>>>(maps, coef, out, L, nbatch, stages,
+                                                           device_status_word());
+    return cudaGetLastError() == cudaSuccess;
+    }
+}
+
 }  // namespace trid
