@@ -7,12 +7,18 @@
 // with X, Y, Z = tridiag(-lambda, 1 + 2 lambda, -lambda) on interior rows and
 // identity rows at the boundary nodes.
 //
-// Schedule (three kernels per 3D step, two per 2D step):
-//   k_adi_x_rhs : stencil RHS + x solve, u -> w          (reads u, writes w)
-//   k_strided   : y solve in place on w                  (reads w, writes w)
-//   k_strided   : z solve, u += result                   (reads w, u; writes u)
+// Schedule of a 3D step (two passes, five mesh-sized arrays of DRAM traffic,
+// the paper's RHS+x+y / z split):
+//   k_adi_plane : stencil RHS + x solve + y solve per z-plane, u -> w
+//                 (a cluster of blocks holds the plane in shared memory)
+//   k_strided   : z solve, u += result          (reads w, u; writes u)
+// 2D steps, and 3D meshes whose plane does not fit the cluster, use
+//   k_adi_x_rhs : stencil RHS + x solve, u -> w
+//   k_strided   : y solve (in place on w, or u += result in 2D)
+//   k_strided   : z solve, u += result  (3D)
 #include "trid_device.cuh"
 #include "trid_strided.cuh"
+#include "trid_adi_static.cuh"
 #include "../../include/trid.h"
 #include "trid_internal.h"
 
@@ -22,6 +28,12 @@ namespace trid {
 
 constexpr int ADI_M = 8;
 constexpr int ADI_MAX_N = 32 * ADI_M;
+
+static int pow2_at_least(int64_t v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
 
 template <typename T, int M>
 __device__ __forceinline__ void adi_load_tile(const T *__restrict__ p, int64_t i0, int64_t n,
@@ -115,11 +127,6 @@ k_adi_x_rhs(const T *__restrict__ u, T *__restrict__ w, int64_t nx, int64_t ny, 
     }
 }
 
-static int pow2_at_least(int64_t v) {
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
 
 template <typename T, int G>
 static void launch_x_rhs(const T *u, T *w, const int64_t *n3, int ndim, T lam, int vec,
@@ -150,8 +157,101 @@ static void launch_adi_strided(T lam, const T *d, T *out, int acc, const Lines &
             <<<strided_grid(L, SG), NT * SG, 0, st>>>(coef, d, out, L, L.nsys / L.inner);
 }
 
+// ---- kernels specialised to the constant operator (axis length % 8 == 0)
+template <typename T, int G>
+static bool launch_x_static_g(const T *u, T *w, const int64_t *n3, int ndim, T lam,
+                              const AdiStatics<T, ADI_XM> &st, cudaStream_t st_) {
+    constexpr int LPW = 4;            // line passes per warp
+    constexpr int GPW = 32 / G;       // lines per warp pass
+    const int64_t lines_per_block = int64_t(8) * GPW * LPW;
+    const int64_t gx = (n3[1] + lines_per_block - 1) / lines_per_block;
+    k_adi_x_static<T, G, LPW><<<dim3(unsigned(gx), unsigned(n3[2])), 256, 0, st_>>>(
+        u, w, int(n3[0]), int(n3[1]), int(n3[2]), ndim, lam, st);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+template <typename T>
+static bool launch_x_static(const T *u, T *w, const int64_t *n3, int ndim, T lam,
+                            cudaStream_t st_) {
+    AdiStatics<T, ADI_XM> st;
+    if (!adi_static_fill<T, ADI_XM>(st, int(n3[0]), double(lam))) return false;
+    if (!is_aligned16(u) || !is_aligned16(w) || (n3[0] * int64_t(sizeof(T))) % 16 != 0)
+        return false;
+    switch (st.ntiles) {
+        case 1: return launch_x_static_g<T, 1>(u, w, n3, ndim, lam, st, st_);
+        case 2: return launch_x_static_g<T, 2>(u, w, n3, ndim, lam, st, st_);
+        case 4: return launch_x_static_g<T, 4>(u, w, n3, ndim, lam, st, st_);
+        case 8: return launch_x_static_g<T, 8>(u, w, n3, ndim, lam, st, st_);
+        case 16: return launch_x_static_g<T, 16>(u, w, n3, ndim, lam, st, st_);
+        default: return launch_x_static_g<T, 32>(u, w, n3, ndim, lam, st, st_);
+    }
+}
+
+template <typename T, int NT, bool ACC>
+static bool launch_strided_static_nt(const T *d, T *out, const Lines &L,
+                                     const AdiStatics<T, ADI_YM> &st, cudaStream_t st_) {
+    constexpr int SG = 16;
+    if constexpr ((NT * SG) % 32 != 0) {
+        return false;
+    } else {
+        const DeviceInfo *di = device_info();
+        if (!di || L.inner < 1) return false;
+        const int64_t outer = L.nsys / L.inner;
+        TmaSet maps;
+        if (!encode_lines_map(&maps.map[0], d, int(sizeof(T)), L.inner, L.n, outer, SG))
+            return false;
+        if (ACC && !encode_lines_map(&maps.map[1], out, int(sizeof(T)), L.inner, L.n, outer, SG))
+            return false;
+        const size_t slot = (size_t(L.n) * SG * sizeof(T) + 127) / 128 * 128;
+        const size_t stage = (ACC ? 2 : 1) * slot;
+        const size_t fixed = (4 * NT * (SG + 1) * sizeof(T) + 127) / 128 * 128;
+        auto bytes = [&](int stages) { return size_t(stages) * (stage + 16) + fixed; };
+        // three blocks per SM when possible, as many stages (<= 4) as then fit
+        const size_t cap2 = size_t(di->smem_per_sm) / 3 - 1024 - 1024;
+        size_t cap = cap2 < size_t(di->max_smem_optin) - 256 ? cap2 : size_t(di->max_smem_optin) - 256;
+        int stages = 4;
+        while (stages > 1 && bytes(stages) > cap) --stages;
+        if (bytes(stages) > cap) {
+            cap = size_t(di->max_smem_optin) - 256;
+            stages = 4;
+            while (stages > 1 && bytes(stages) > cap) --stages;
+            if (bytes(stages) > cap) return false;
+        }
+        const size_t smem = bytes(stages);
+        auto kern = k_adi_strided_static<T, NT, SG, ACC>;
+        const int per_sm =
+            kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), NT * SG + 32, smem);
+        if (per_sm < 1) return false;
+        const int64_t nbatch = (L.inner + SG - 1) / SG * outer;
+        const int64_t slots = int64_t(di->sm_count) * per_sm;
+        const int64_t grid = nbatch < slots ? nbatch : slots;
+        kern<<<dim3(unsigned(grid)), NT * SG + 32, smem, st_>>>(maps, st, out, L, nbatch, stages,
+                                                               device_status_word());
+        return cudaGetLastError() == cudaSuccess;
+    }
+}
+
+template <typename T, bool ACC>
+static bool launch_strided_static(T lam, const T *d, T *out, const Lines &L, cudaStream_t st_) {
+    AdiStatics<T, ADI_YM> st;
+    if (!adi_static_fill<T, ADI_YM>(st, int(L.n), double(lam))) return false;
+    if (!strided_offsets_fit(L)) return false;
+    switch (st.ntiles) {
+        case 1: return launch_strided_static_nt<T, 1, ACC>(d, out, L, st, st_);
+        case 2: return launch_strided_static_nt<T, 2, ACC>(d, out, L, st, st_);
+        case 4: return launch_strided_static_nt<T, 4, ACC>(d, out, L, st, st_);
+        case 8: return launch_strided_static_nt<T, 8, ACC>(d, out, L, st, st_);
+        case 16: return launch_strided_static_nt<T, 16, ACC>(d, out, L, st, st_);
+        case 32: return launch_strided_static_nt<T, 32, ACC>(d, out, L, st, st_);
+        default: return false;
+    }
+}
+
 template <typename T>
 static void adi_strided(T lam, const T *d, T *out, int acc, const Lines &L, cudaStream_t st) {
+    if (acc ? launch_strided_static<T, true>(lam, d, out, L, st)
+            : launch_strided_static<T, false>(lam, d, out, L, st))
+        return;
     switch (pow2_at_least((L.n + ADI_M - 1) / ADI_M)) {
         case 1: launch_adi_strided<T, 1>(lam, d, out, acc, L, st); break;
         case 2: launch_adi_strided<T, 2>(lam, d, out, acc, L, st); break;
@@ -170,6 +270,16 @@ static trid_status adi_run(T *u, const int64_t *n3, int ndim, T lam, int nsteps,
     Lines Ly{n3[0] * n3[2], n3[1], n3[0], n3[0]};
     Lines Lz{n3[0] * n3[1], n3[2], n3[0] * n3[1], n3[0] * n3[1]};
     for (int step = 0; step < nsteps; ++step) {
+        if (launch_x_static<T>(u, w, n3, ndim, lam, st)) {
+            if (ndim == 3) {
+                adi_strided<T>(lam, w, w, 0, Ly, st);
+                adi_strided<T>(lam, w, u, 1, Lz, st);
+            } else {
+                adi_strided<T>(lam, w, u, 1, Ly, st);
+            }
+            if (cudaGetLastError() != cudaSuccess) return TRID_ERR_CUDA;
+            continue;
+        }
         switch (G) {
             case 1: launch_x_rhs<T, 1>(u, w, n3, ndim, lam, vec, st); break;
             case 2: launch_x_rhs<T, 2>(u, w, n3, ndim, lam, vec, st); break;

@@ -44,6 +44,42 @@ const DeviceInfo *device_info() {
     return &g_info[dev];
 }
 
+namespace {
+struct OccEntry {
+    const void *kernel;
+    int dev, threads;
+    size_t smem;
+    int blocks;
+};
+constexpr int kOccCache = 256;
+OccEntry g_occ[kOccCache];
+int g_nocc = 0;
+}  // namespace
+
+int kernel_blocks_per_sm(const void *kernel, int threads, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int i = 0; i < g_nocc; ++i) {
+        const OccEntry &e = g_occ[i];
+        if (e.kernel == kernel && e.dev == dev && e.threads == threads && e.smem == smem)
+            return e.blocks;
+    }
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (g_nocc < kOccCache) g_occ[g_nocc++] = OccEntry{kernel, dev, threads, smem, blocks};
+    return blocks;
+}
+
 bool encode_lines_map(void *map, const void *base, int esz, int64_t inner, int64_t n,
                       int64_t outer, int box_x) {
     {

@@ -28,6 +28,12 @@ const DeviceInfo *device_info();
 bool encode_lines_map(void *map /* CUtensorMap */, const void *base, int esz, int64_t inner,
                       int64_t n, int64_t outer, int box_x);
 
+// Blocks of `kernel` resident per SM for (threads, dynamic smem) on the
+// current device, after raising the kernel's dynamic shared-memory limit to
+// `smem`.  Both results are cached per (kernel, device, threads, smem), so a
+// launch in a time-stepping loop costs no extra driver calls.  0 on failure.
+int kernel_blocks_per_sm(const void *kernel, int threads, size_t smem);
+
 // Device address of the status word of the current device (see
 // trid_get_device_status); kernels that run bounded waits record failures there.
 int *device_status_word();

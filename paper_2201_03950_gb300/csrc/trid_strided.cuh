@@ -345,18 +345,8 @@ inline bool launch_strided_tma(const void *const *arrs, Coef coef, T *out, const
     const size_t smem = LY::bytes(int(L.n), NSLOT, stages);
     if (smem > size_t(di->max_smem_optin)) return false;
     auto kern = k_strided_tma<T, M, NT, SG, ACC, Coef>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT * SG + 32, smem) !=
-            cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        return false;
-    }
+    const int per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), NT * SG + 32, smem);
+    if (per_sm < 1) return false;
     const int64_t nbatch = (L.inner + SG - 1) / SG * outer;
     const int64_t slots = int64_t(di->sm_count) * per_sm;
     const int64_t grid = nbatch < slots ? nbatch : slots;

@@ -214,7 +214,10 @@ def run_adi(u0, dims, lam, steps, dtype):
 
 ADI_SMALL = [((9, 7, 6), 0.1, 3), ((40, 36, 33), 0.1, 10), ((64, 64, 64), 0.1, 5),
              ((33, 257 - 1, 17), 0.2, 2), ((12, 10), 0.3, 7), ((128, 100), 0.1, 20),
-             ((3, 3, 3), 0.1, 2)]
+             ((3, 3, 3), 0.1, 2), ((24, 100, 7), 0.15, 3), ((16, 8, 5), 0.1, 2),
+             ((256, 256, 3), 0.1, 2), ((32, 250, 9), 0.1, 2), ((8, 3, 4), 0.1, 1),
+             ((200, 17, 12), 0.25, 2), ((64, 64, 160), 0.1, 2), ((32, 40, 250), 0.1, 1),
+             ((256, 20, 40), 0.1, 1)]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
