@@ -101,6 +101,35 @@ trid_status trid_solve_batch_ws(const void *a, const void *b, const void *c, voi
                                 void *workspace, size_t workspace_bytes, trid_stream_t stream);
 
 /*
+ * Allocation-free batched solve.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library call cudaMalloc -- a
+ * framework whose own memory pool already holds the device memory, or a
+ * latency-critical loop that must not pay the device-wide synchronisation of
+ * growing trid_solve_batch's scratch pool.
+ *
+ * Same arguments and results as trid_solve_batch.  Systems longer than 256
+ * need scratch (trid_solve_workspace_bytes); here it comes from one fixed
+ * device array of TRID_NOALLOC_SCRATCH_BYTES (32 MiB) that the library holds
+ * on every GPU that loads it, until the process exits.  The call never
+ * allocates or frees device memory.
+ *   - Problems needing more scratch than TRID_NOALLOC_SCRATCH_BYTES are
+ *     rejected with TRID_ERR_ALLOC before anything is launched (use
+ *     trid_solve_batch_ws with your own buffer for those).
+ *   - The first call on a device that needs scratch looks up the array's
+ *     device address (cudaGetSymbolAddress); make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the one array.  Calls whose work overlaps
+ *     on the GPU (different streams, no ordering between them) race on it and
+ *     may return wrong results; order them, e.g. issue them on one stream.
+ *   - The array keeps the last call's contents; the solve overwrites every
+ *     scratch value before reading it, so nothing needs clearing.
+ */
+#define TRID_NOALLOC_SCRATCH_BYTES (32u << 20)
+trid_status trid_solve_batch_noalloc(const void *a, const void *b, const void *c, void *d,
+                                     void *u, const int64_t *dims, int ndim, int solve_dim,
+                                     trid_dtype dtype, trid_stream_t stream);
+
+/*
  * ADI heat-diffusion time steps, Section 4.1, Algorithm "adi": per step,
  * d = lambda * (sum of the 2*ndim axis neighbours of u - 2*ndim*u) on interior
  * nodes (0 on boundary nodes); d <- X^{-1} d; d <- Y^{-1} d; [d <- Z^{-1} d;]

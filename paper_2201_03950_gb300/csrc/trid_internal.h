@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 #include "../../include/trid.h"
 
 namespace trid {
@@ -33,6 +35,13 @@ bool encode_lines_map(void *map /* CUtensorMap */, const void *base, int esz, in
 // `smem`.  Both results are cached per (kernel, device, threads, smem), so a
 // launch in a time-stepping loop costs no extra driver calls.  0 on failure.
 int kernel_blocks_per_sm(const void *kernel, int threads, size_t smem);
+
+// Batched solve with caller-chosen scratch (checks arguments on the host;
+// TRID_ERR_ALLOC without launching when scratch_bytes < need).
+trid_status solve_with_scratch(const void *a, const void *b, const void *c, void *d, void *u,
+                               const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
+                               void *scratch, size_t scratch_bytes, size_t &need,
+                               cudaStream_t st);
 
 // Device address of the status word of the current device (see
 // trid_get_device_status); kernels that run bounded waits record failures there.

@@ -419,9 +419,32 @@ static trid_status solve_dispatch(const void *a, const void *b, const void *c, v
                                out, acc, L, ws, ws_bytes, st);
 }
 
+// Argument check, scratch size and dispatch for a caller that supplies its own
+// scratch (used by the allocation-free entry point).  `need` receives the
+// scratch bytes the problem requires; nothing is launched when the returned
+// status is not TRID_OK or when `scratch_bytes < need`.
+trid_status solve_with_scratch(const void *a, const void *b, const void *c, void *d, void *u,
+                               const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
+                               void *scratch, size_t scratch_bytes, size_t &need,
+                               cudaStream_t st);
+
 size_t solve_ws_bytes(const Lines &L, trid_dtype dtype) {
     return dtype == TRID_F32 ? long_ws_bytes<float>(L.nsys, L.n)
                              : long_ws_bytes<double>(L.nsys, L.n);
+}
+
+trid_status solve_with_scratch(const void *a, const void *b, const void *c, void *d, void *u,
+                               const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
+                               void *scratch, size_t scratch_bytes, size_t &need,
+                               cudaStream_t st) {
+    Lines L;
+    size_t esz;
+    need = 0;
+    trid_status s = check_solve_args(a, b, c, d, u, dims, ndim, solve_dim, dtype, L, esz);
+    if (s != TRID_OK || L.nsys == 0 || L.n == 0) return s;
+    need = solve_ws_bytes(L, dtype);
+    if (need > scratch_bytes) return TRID_ERR_ALLOC;
+    return solve_dispatch(a, b, c, d, u, L, dtype, static_cast<char *>(scratch), scratch_bytes, st);
 }
 
 }  // namespace trid

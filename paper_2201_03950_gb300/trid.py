@@ -54,6 +54,7 @@ def _bind(L):
     sigs = {
         "trid_solve_batch": ([P, P, P, P, P, P, i32, i32, i32, P], i32),
         "trid_solve_batch_ws": ([P, P, P, P, P, P, i32, i32, i32, P, sz, P], i32),
+        "trid_solve_batch_noalloc": ([P, P, P, P, P, P, i32, i32, i32, P], i32),
         "trid_solve_workspace_bytes": ([P, i32, i32, i32], sz),
         "adi_step": ([P, P, i32, f64, i32, i32, P, sz, P], i32),
         "adi_workspace_bytes": ([P, i32, i32], sz),
@@ -122,6 +123,23 @@ def solve(a, b, c, d, dims, solve_dim: int, u=None, workspace=None, stream=None)
                                    workspace.numel() * workspace.element_size(), _stream(stream))
     if st != 0:
         raise TridError(st, "trid_solve_batch")
+    return u if u is not None else d
+
+
+def solve_noalloc(a, b, c, d, dims, solve_dim: int, u=None, stream=None):
+    """As ``solve``, through trid_solve_batch_noalloc: for callers that must not
+    let the library allocate device memory (the long-system scratch comes from
+    a fixed 32 MiB device array; see include/trid.h)."""
+    numel = 1
+    for v in dims:
+        numel *= int(v)
+    _check_tensors((a, b, c, d, u), d, numel)
+    L = load()
+    dc, nd = _dims(dims)
+    st = L.trid_solve_batch_noalloc(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(u), dc, nd,
+                                    solve_dim, _dtype(d), _stream(stream))
+    if st != 0:
+        raise TridError(st, "trid_solve_batch_noalloc")
     return u if u is not None else d
 
 
