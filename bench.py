@@ -45,11 +45,13 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the 4096^2 long-system measurement")
     p.add_argument("--dtype", choices=["f32", "f64"], default="f32",
                    help="f64 runs the same step in FP64 (reported separately; the headline is f32)")
     return p.parse_args()
@@ -93,7 +95,7 @@ def profiled_traffic(kernel_key: str):
 
 
 class Clocks:
-    """Samples nvidia-smi every 200 ms while the timed region runs."""
+    """Samples nvidia-smi every 50 ms from the warm-up through the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -109,7 +111,7 @@ class Clocks:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.tmp, stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
@@ -198,14 +200,14 @@ def run_ours(args):
         if record is not None:
             record.append(evs)
 
+    clocks = Clocks(local)
+    clocks.start()
     for _ in range(args.warmup):
         one_step(None)
-    clocks = Clocks(local)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     recs = []
     t_wall = time.perf_counter()
     for _ in range(args.steps):
@@ -226,6 +228,33 @@ def run_ours(args):
         ms_step = float(t.item())
     step_bytes = sum(nbytes.values())
     value = world * step_bytes / (ms_step * 1e-3) / 1e9
+
+    # ---- secondary workload: 4096^2 FP32, few long systems (tiled Thomas-PCR
+    #      passes), along x and y; same restore + flush protocol, mean of 5
+    secondary = {}
+    if args.dtype == "f32" and not args.no_secondary:
+        dims2 = (4096, 4096)
+        tot2 = dims2[0] * dims2[1]
+        a2, b2, c2, d2 = inputs.dominant_system((tot2,), seed=11 + rank, dtype=np.float32)
+        ta2, tb2, tc2, td2_0 = (torch.from_numpy(v).to(dev) for v in (a2, b2, c2, d2))
+        td2 = torch.empty_like(td2_0)
+        for k, name in ((0, "solve_4096sq_x"), (1, "solve_4096sq_y")):
+            times = []
+            for it in range(6):
+                td2.copy_(td2_0)
+                flush.fill_(it + 3)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                trid.solve(ta2, tb2, tc2, td2, dims2, k, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it:
+                    times.append(e0.elapsed_time(e1))
+            ms = statistics.mean(times)
+            nb = metrics.solve_bytes(tot2, 4)
+            secondary[name] = {"us": round(ms * 1e3, 2), "GBps": round(nb / (ms * 1e-3) / 1e9, 1),
+                               "frac": round(nb / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
+        del ta2, tb2, tc2, td2_0, td2
 
     # ---- ADI time stepping as a solver runs it: 100 steps captured in one
     #      CUDA graph and replayed (no flush between steps), per step
@@ -297,6 +326,7 @@ def run_ours(args):
                    "l2": "flushed before every timed call (256 MiB write); inputs 256 MiB per solve",
                    "timing": "CUDA events per call on the launching stream, summed per step"},
         "per_call": solve_frac,
+        "secondary": secondary,
         "adi_step_ms": round(means["adi_step"], 4),
         "adi_step_ms_graph100": (round(adi_graph_ms, 4) if isinstance(adi_graph_ms, float)
                                  else adi_graph_ms),
