@@ -101,6 +101,38 @@ trid_status trid_solve_batch_ws(const void *a, const void *b, const void *c, voi
                                 void *workspace, size_t workspace_bytes, trid_stream_t stream);
 
 /*
+ * Batch of independent systems of different lengths, solved in one
+ * persistent launch (the batched solves of Section 4 generalised to uneven
+ * lengths; long systems use the tiled Thomas-PCR hybrid of Section 3.1).
+ *
+ *   offsets    DEVICE int64 array of nsys + 1 entries: system k occupies rows
+ *              [offsets[k], offsets[k+1]) of a, b, c, d (and u), which are
+ *              dense arrays of `total` elements.  Systems may have length 0;
+ *              a system with rows outside [0, total) or longer than max_len
+ *              is skipped and TRID_ERR_INVALID_ARG is recorded in the device
+ *              status word (trid_get_device_status).
+ *   total      host: number of elements of each array.
+ *   max_len    host: an upper bound of the system lengths; it sizes the
+ *              shared-memory reduced systems (TRID_ERR_UNSUPPORTED when they
+ *              do not fit: about 56K rows in FP32, 28K in FP64).
+ *   u, dtype, stream  as for trid_solve_batch (u == NULL: in place in d).
+ *   workspace  caller device scratch of trid_solve_varlen_workspace_bytes(nsys)
+ *              bytes, 256-byte aligned (work order and queue counters; fully
+ *              rewritten by every call, so calls on one workspace must not
+ *              overlap on the GPU).
+ * Two kernels are enqueued (a planning pass that orders the systems longest
+ * first, then the persistent solve); nothing is allocated and the host does
+ * not wait.
+ */
+trid_status trid_solve_batch_varlen(const void *a, const void *b, const void *c, void *d, void *u,
+                                    const int64_t *offsets, int64_t nsys, int64_t total,
+                                    int64_t max_len, trid_dtype dtype, void *workspace,
+                                    size_t workspace_bytes, trid_stream_t stream);
+
+/* Workspace bytes trid_solve_batch_varlen needs for nsys systems. */
+size_t trid_solve_varlen_workspace_bytes(int64_t nsys);
+
+/*
  * Allocation-free batched solve.  The paper has no counterpart: this entry
  * point exists for callers that cannot let a library call cudaMalloc -- a
  * framework whose own memory pool already holds the device memory, or a

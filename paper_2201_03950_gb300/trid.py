@@ -56,6 +56,8 @@ def _bind(L):
         "trid_solve_batch_ws": ([P, P, P, P, P, P, i32, i32, i32, P, sz, P], i32),
         "trid_solve_batch_noalloc": ([P, P, P, P, P, P, i32, i32, i32, P], i32),
         "trid_solve_workspace_bytes": ([P, i32, i32, i32], sz),
+        "trid_solve_batch_varlen": ([P, P, P, P, P, P, i64, i64, i64, i32, P, sz, P], i32),
+        "trid_solve_varlen_workspace_bytes": ([i64], sz),
         "adi_step": ([P, P, i32, f64, i32, i32, P, sz, P], i32),
         "adi_workspace_bytes": ([P, i32, i32], sz),
         "trid_get_device_status": ([P], i32),
@@ -140,6 +142,31 @@ def solve_noalloc(a, b, c, d, dims, solve_dim: int, u=None, stream=None):
                                     solve_dim, _dtype(d), _stream(stream))
     if st != 0:
         raise TridError(st, "trid_solve_batch_noalloc")
+    return u if u is not None else d
+
+
+def varlen_workspace_bytes(nsys: int) -> int:
+    return int(load().trid_solve_varlen_workspace_bytes(int(nsys)))
+
+
+def solve_varlen(a, b, c, d, offsets, max_len: int, u=None, workspace=None, stream=None):
+    """Batch of systems of different lengths: system k occupies rows
+    [offsets[k], offsets[k+1]) (offsets: int64 CUDA tensor of nsys + 1)."""
+    import torch
+    total = d.numel()
+    _check_tensors((a, b, c, d, u), d, total)
+    if not (offsets.is_cuda and offsets.dtype == torch.int64 and offsets.is_contiguous()):
+        raise ValueError("offsets must be a contiguous int64 CUDA tensor")
+    nsys = offsets.numel() - 1
+    L = load()
+    if workspace is None:
+        workspace = torch.empty(varlen_workspace_bytes(max(nsys, 0)), dtype=torch.uint8,
+                                device=d.device)
+    st = L.trid_solve_batch_varlen(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(u), _ptr(offsets),
+                                   int(nsys), int(total), int(max_len), _dtype(d), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream))
+    if st != 0:
+        raise TridError(st, "trid_solve_batch_varlen")
     return u if u is not None else d
 
 

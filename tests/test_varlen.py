@@ -1,0 +1,138 @@
+"""Uneven batches (trid_solve_batch_varlen) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_03950_gb300 import inputs, trid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {np.float32: 1e-5, np.float64: 1e-12}
+
+
+def per_system_err(x, ref, off):
+    worst = 0.0
+    for k in range(len(off) - 1):
+        s, e = off[k], off[k + 1]
+        if e <= s:
+            continue
+        r = np.asarray(ref[s:e], dtype=np.float64)
+        g = np.asarray(x[s:e], dtype=np.float64)
+        worst = max(worst, float(np.max(np.abs(g - r)) / max(np.max(np.abs(r)), 1e-300)))
+    return worst
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2201_03950_gb300 import build
+    build.build()
+    trid.load()
+
+
+def run(lengths, dtype, seed=0, accumulate=False, max_len=None):
+    lengths = np.asarray(lengths, dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    total = int(off[-1])
+    a, b, c, d = inputs.dominant_system((max(total, 1),), seed=seed, dtype=dtype)
+    a, b, c, d = a[:total], b[:total], c[:total], d[:total]
+    ref = oracle.solve_varlen(a, b, c, d, off)
+    ta, tb, tc, td = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (a, b, c, d))
+    toff = torch.from_numpy(off).cuda()
+    ml = int(lengths.max()) if max_len is None else max_len
+    if accumulate:
+        u0 = inputs.random_rhs((total,), seed=seed + 5, dtype=dtype)
+        tu = torch.from_numpy(u0).cuda()
+        trid.solve_varlen(ta, tb, tc, td, toff, ml, u=tu)
+        torch.cuda.synchronize()
+        got = tu.cpu().numpy().astype(np.float64) - u0.astype(np.float64)
+    else:
+        trid.solve_varlen(ta, tb, tc, td, toff, ml)
+        torch.cuda.synchronize()
+        got = td.cpu().numpy()
+    return got, ref, off
+
+
+EDGE = [1, 2, 3, 0, 5, 8, 9, 16, 31, 255, 256, 257, 300, 511, 512, 513, 1000, 2047, 2048, 2049,
+        4100, 16384, 20000, 0, 7]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+def test_varlen_edge_lengths(dtype):
+    got, ref, off = run(EDGE, dtype, seed=1)
+    assert np.all(np.isfinite(got))
+    assert per_system_err(got, ref, off) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+def test_varlen_loguniform(dtype):
+    lengths = inputs.loguniform_lengths(300, 16, 16384, seed=4)
+    got, ref, off = run(lengths, dtype, seed=2)
+    assert per_system_err(got, ref, off) <= TOL[dtype]
+
+
+def test_varlen_accumulate_and_many_short():
+    lengths = np.concatenate([np.full(3000, 17), [4096, 300], np.arange(1, 60)])
+    got, ref, off = run(lengths, np.float32, seed=3, accumulate=True)
+    assert per_system_err(got, ref, off) <= 2e-5
+
+
+def test_varlen_invalid_system_is_flagged_and_skipped():
+    # system 1 points past the arrays; its neighbours are still solved
+    lengths = np.array([40, 50, 60], dtype=np.int64)
+    off = np.array([0, 40, 1_000_000, 150], dtype=np.int64)  # offsets not monotone for system 1/2
+    total = 150
+    a, b, c, d = inputs.dominant_system((total,), seed=9, dtype=np.float32)
+    ta, tb, tc, td = (torch.from_numpy(v).cuda() for v in (a, b, c, d))
+    toff = torch.from_numpy(off).cuda()
+    assert trid.device_status() == 0
+    trid.solve_varlen(ta, tb, tc, td, toff, 64)
+    torch.cuda.synchronize()
+    assert trid.device_status() == 1  # TRID_ERR_INVALID_ARG recorded, then cleared
+    x = td.cpu().numpy()
+    ref0 = oracle.thomas(a[:40], b[:40], c[:40], d[:40])
+    assert per_system_err(x[:40], ref0, [0, 40]) <= 1e-5
+    assert trid.device_status() == 0
+
+
+def test_varlen_empty_and_too_long_rejected_on_host():
+    t = torch.zeros(8, device="cuda")
+    off = torch.zeros(1, dtype=torch.int64, device="cuda")
+    trid.solve_varlen(t, t, t, t, off, 8)  # nsys = 0: nothing to do
+    with pytest.raises(trid.TridError):
+        off2 = torch.tensor([0, 8], dtype=torch.int64, device="cuda")
+        trid.solve_varlen(t, t, t, t, off2, 10_000_000)  # reduced systems do not fit
+
+
+def test_varlen_full_size_config_sampled():
+    """8192 systems, lengths log-uniform in [16, 16384], FP32: sampled systems
+    against the oracle and the residual over every row."""
+    lengths = inputs.loguniform_lengths(8192, 16, 16384, seed=0)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    total = int(off[-1])
+    a, b, c, d = inputs.dominant_system((total,), seed=0, dtype=np.float32)
+    ta, tb, tc, td = (torch.from_numpy(v).cuda() for v in (a, b, c, d))
+    td0 = td.clone()
+    trid.solve_varlen(ta, tb, tc, td, torch.from_numpy(off).cuda(), 16384)
+    torch.cuda.synchronize()
+    x = td.cpu().numpy()
+    rng = np.random.default_rng(1)
+    pick = np.unique(np.concatenate([rng.choice(8192, 150, replace=False),
+                                     [int(np.argmax(lengths)), int(np.argmin(lengths))]]))
+    worst = 0.0
+    for k in pick:
+        s, e = off[k], off[k + 1]
+        ref = oracle.thomas(a[s:e], b[s:e], c[s:e], d[s:e])
+        worst = max(worst, per_system_err(x[s:e], ref, [0, e - s]))
+    assert worst <= 1e-5
+    # residual |A x - d| over all systems, in FP64 with plain torch ops
+    A, B, C, D, X = (t.double() for t in (ta, tb, tc, td0, td))
+    r = B * X
+    first = torch.zeros(total, dtype=torch.bool, device="cuda")
+    first[torch.from_numpy(off[:-1]).cuda()] = True
+    last = torch.zeros(total, dtype=torch.bool, device="cuda")
+    last[torch.from_numpy(off[1:] - 1).cuda()] = True
+    r[1:] += torch.where(first[1:], 0.0, A[1:] * X[:-1])
+    r[:-1] += torch.where(last[:-1], 0.0, C[:-1] * X[1:])
+    res = ((r - D).abs().max() / ((A.abs() + B.abs() + C.abs()).max() * X.abs().max() + D.abs().max())).item()
+    assert res <= 1e-5
