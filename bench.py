@@ -256,6 +256,38 @@ def run_ours(args):
                                "frac": round(nb / (ms * 1e-3) / 1e9 / peaks()[0], 4)}
         del ta2, tb2, tc2, td2_0, td2
 
+        # adjoint of the 256^3 solves (g_d = A^-T g_x and the coefficient
+        # gradients: 9 words per unknown -- a, b, c, x, g_x read; g_a, g_b,
+        # g_c, g_d written), against the forward GB/s of the same axis
+        tgx = torch.from_numpy(inputs.random_rhs((total,), seed=31 + rank, dtype=np.float32)).to(dev)
+        tx = td0.clone()
+        outs = [torch.empty_like(tx) for _ in range(4)]
+        L = trid.load()
+        import ctypes
+        for k, name in ((0, "adjoint_x"), (2, "adjoint_z")):
+            times = []
+            dc = (ctypes.c_int64 * 3)(*DIMS)
+            for it in range(6):
+                flush.fill_(it + 5)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st_ = L.trid_solve_batch_adjoint(*(ctypes.c_void_p(t.data_ptr()) for t in
+                                                   (ta, tb, tc, tx, tgx, *outs)), dc, 3, k, 0,
+                                                 None, 0, ctypes.c_void_p(stream.cuda_stream))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                assert st_ == 0
+                if it:
+                    times.append(e0.elapsed_time(e1))
+            ms = statistics.mean(times)
+            nb = 9 * total * 4
+            gbs = nb / (ms * 1e-3) / 1e9
+            fwd = nbytes[f"solve_{'xyz'[k]}"] / (statistics.mean(per[f"solve_{'xyz'[k]}"]) * 1e-3) / 1e9
+            secondary[name] = {"us": round(ms * 1e3, 2), "GBps": round(gbs, 1),
+                               "frac": round(gbs / peaks()[0], 4),
+                               "ratio_to_forward_GBps": round(gbs / fwd, 3)}
+        del tgx, tx, outs
+
         # uneven batch: 8192 systems, lengths log-uniform in [16, 16384], FP32,
         # planning + persistent solve captured in one CUDA graph and replayed
         lengths = inputs.loguniform_lengths(8192, 16, 16384, seed=rank)

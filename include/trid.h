@@ -101,6 +101,33 @@ trid_status trid_solve_batch_ws(const void *a, const void *b, const void *c, voi
                                 void *workspace, size_t workspace_bytes, trid_stream_t stream);
 
 /*
+ * Adjoint of trid_solve_batch, for reverse-mode differentiation of
+ * x = A^{-1} d along a mesh axis (the solve is the one Section 2 defines; its
+ * adjoint is standard linear algebra, which the paper does not discuss).
+ * Given the forward solution x and g_x = dL/dx (device arrays, same layout as
+ * the forward call), it writes
+ *   g_d = A^{-T} g_x      (A^T: sub-diagonal c_{i-1}, diagonal b_i,
+ *                          super-diagonal a_{i+1}),
+ *   g_a_i = -g_d_i x_{i-1},  g_b_i = -g_d_i x_i,  g_c_i = -g_d_i x_{i+1},
+ * with g_a = 0 on each system's first row and g_c = 0 on its last row (those
+ * entries are not part of A).  g_a, g_b, g_c may be NULL (not written); g_d is
+ * required.  Outputs must not alias each other or the inputs.  a at each
+ * system's first row and c at its last row are not read.
+ * Systems longer than 256 need `workspace` of
+ * trid_adjoint_workspace_bytes(...) bytes (256-byte aligned); else it may be
+ * NULL.  Never allocates.
+ */
+trid_status trid_solve_batch_adjoint(const void *a, const void *b, const void *c, const void *x,
+                                     const void *g_x, void *g_a, void *g_b, void *g_c, void *g_d,
+                                     const int64_t *dims, int ndim, int solve_dim,
+                                     trid_dtype dtype, void *workspace, size_t workspace_bytes,
+                                     trid_stream_t stream);
+
+/* Scratch bytes trid_solve_batch_adjoint needs (0 for systems <= 256). */
+size_t trid_adjoint_workspace_bytes(const int64_t *dims, int ndim, int solve_dim,
+                                    trid_dtype dtype);
+
+/*
  * Batch of independent systems of different lengths, solved in one
  * persistent launch (the batched solves of Section 4 generalised to uneven
  * lengths; long systems use the tiled Thomas-PCR hybrid of Section 3.1).

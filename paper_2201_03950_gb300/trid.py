@@ -58,6 +58,8 @@ def _bind(L):
         "trid_solve_workspace_bytes": ([P, i32, i32, i32], sz),
         "trid_solve_batch_varlen": ([P, P, P, P, P, P, i64, i64, i64, i32, P, sz, P], i32),
         "trid_solve_varlen_workspace_bytes": ([i64], sz),
+        "trid_solve_batch_adjoint": ([P, P, P, P, P, P, P, P, P, P, i32, i32, i32, P, sz, P], i32),
+        "trid_adjoint_workspace_bytes": ([P, i32, i32, i32], sz),
         "adi_step": ([P, P, i32, f64, i32, i32, P, sz, P], i32),
         "adi_workspace_bytes": ([P, i32, i32], sz),
         "trid_get_device_status": ([P], i32),
@@ -143,6 +145,31 @@ def solve_noalloc(a, b, c, d, dims, solve_dim: int, u=None, stream=None):
     if st != 0:
         raise TridError(st, "trid_solve_batch_noalloc")
     return u if u is not None else d
+
+
+def adjoint(a, b, c, x, gx, dims, solve_dim: int, need_coef_grads: bool = True, stream=None):
+    """Gradients of L through x = A^{-1} d along ``solve_dim``: returns
+    (g_a, g_b, g_c, g_d) (the first three None if ``need_coef_grads`` is
+    False).  All arrays are CUDA tensors with the forward call's layout."""
+    import torch
+    numel = 1
+    for v in dims:
+        numel *= int(v)
+    _check_tensors((a, b, c, x, gx), x, numel)
+    L = load()
+    dc, nd = _dims(dims)
+    gd = torch.empty_like(x)
+    ga = torch.empty_like(x) if need_coef_grads else None
+    gb = torch.empty_like(x) if need_coef_grads else None
+    gc = torch.empty_like(x) if need_coef_grads else None
+    nbytes = int(L.trid_adjoint_workspace_bytes(dc, nd, solve_dim, _dtype(x)))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=x.device) if nbytes else None
+    st = L.trid_solve_batch_adjoint(_ptr(a), _ptr(b), _ptr(c), _ptr(x), _ptr(gx), _ptr(ga),
+                                    _ptr(gb), _ptr(gc), _ptr(gd), dc, nd, solve_dim, _dtype(x),
+                                    _ptr(ws), nbytes, _stream(stream))
+    if st != 0:
+        raise TridError(st, "trid_solve_batch_adjoint")
+    return ga, gb, gc, gd
 
 
 def varlen_workspace_bytes(nsys: int) -> int:
