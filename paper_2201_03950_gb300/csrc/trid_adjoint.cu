@@ -43,7 +43,7 @@ template <typename T, int M, int G>
 __global__ void __launch_bounds__(256)
 k_adjoint_lines(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c,
                 const T *__restrict__ x, const T *__restrict__ gx, T *ga, T *gb, T *gc, T *gd,
-                int64_t nsys, int64_t n) {
+                int64_t nsys, int64_t n, int vec_ok) {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -52,23 +52,28 @@ k_adjoint_lines(const T *__restrict__ a, const T *__restrict__ b, const T *__res
     const bool active = sys < nsys;
     const int64_t i0 = int64_t(g) * M;
     const int64_t base = sys * n;
+    const bool vec = active && vec_ok && i0 + M <= n;
 
     T ra[M], rb[M], rc[M], rd[M], rx[M];
+    if (vec) {
+        load_contig_vec<T, M>(a + base + i0, ra);
+        load_contig_vec<T, M>(b + base + i0, rb);
+        load_contig_vec<T, M>(c + base + i0, rc);
+        load_contig_vec<T, M>(gx + base + i0, rd);
+    } else {
 #pragma unroll
-    for (int j = 0; j < M; ++j) {
-        const int64_t i = i0 + j;
-        const bool in = active && i < n;
-        ra[j] = in ? a[base + i] : T(0);  // raw a, shifted below
-        rb[j] = in ? b[base + i] : T(1);
-        rc[j] = in ? c[base + i] : T(0);  // raw c, shifted below
-        rd[j] = in ? gx[base + i] : T(0);
-        rx[j] = in ? x[base + i] : T(0);
+        for (int j = 0; j < M; ++j) {
+            const int64_t i = i0 + j;
+            const bool in = active && i < n;
+            ra[j] = in ? a[base + i] : T(0);  // raw a, shifted below
+            rb[j] = in ? b[base + i] : T(1);
+            rc[j] = in ? c[base + i] : T(0);  // raw c, shifted below
+            rd[j] = in ? gx[base + i] : T(0);
+        }
     }
     // A^T: sub-diagonal at row i is c_{i-1}, super-diagonal is a_{i+1}
     const T c_prev = __shfl_up_sync(FULL, rc[M - 1], 1, G);
     const T a_next = __shfl_down_sync(FULL, ra[0], 1, G);
-    const T x_prev = __shfl_up_sync(FULL, rx[M - 1], 1, G);
-    const T x_next = __shfl_down_sync(FULL, rx[0], 1, G);
     T ta[M], tc[M];
 #pragma unroll
     for (int j = 0; j < M; ++j) {
@@ -78,9 +83,43 @@ k_adjoint_lines(const T *__restrict__ a, const T *__restrict__ b, const T *__res
     }
     T as, cs, ds, ae, ce, de, xs, xe;
     tile_reduce<T, M>(ta, rb, tc, rd, as, cs, ds, ae, ce, de);
+    // x for the gradients, fetched behind the reduced solve
+    if (vec) {
+        load_contig_vec<T, M>(x + base + i0, rx);
+    } else {
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const int64_t i = i0 + j;
+            rx[j] = (active && i < n) ? x[base + i] : T(0);
+        }
+    }
     group_solve<T, G>(as, cs, ds, ae, ce, de, g, xs, xe);
+    const T x_prev = __shfl_up_sync(FULL, rx[M - 1], 1, G);
+    const T x_next = __shfl_down_sync(FULL, rx[0], 1, G);
     tile_substitute<T, M>(ta, tc, rd, xs, xe);
     if (!active) return;
+    if (vec) {
+        T r[M];
+        store_contig_vec<T, M>(gd + base + i0, rd);
+        if (gb) {
+#pragma unroll
+            for (int j = 0; j < M; ++j) r[j] = -rd[j] * rx[j];
+            store_contig_vec<T, M>(gb + base + i0, r);
+        }
+        if (ga) {
+#pragma unroll
+            for (int j = 0; j < M; ++j)
+                r[j] = (i0 + j > 0) ? -rd[j] * ((j == 0) ? x_prev : rx[j - 1]) : T(0);
+            store_contig_vec<T, M>(ga + base + i0, r);
+        }
+        if (gc) {
+#pragma unroll
+            for (int j = 0; j < M; ++j)
+                r[j] = (i0 + j < n - 1) ? -rd[j] * ((j == M - 1) ? x_next : rx[j + 1]) : T(0);
+            store_contig_vec<T, M>(gc + base + i0, r);
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < M; ++j) {
         const int64_t i = i0 + j;
@@ -202,8 +241,14 @@ static void launch_adj_lines(const T *a, const T *b, const T *c, const T *x, con
                              T *gb, T *gc, T *gd, const Lines &L, cudaStream_t st) {
     const int64_t warps = (L.nsys + (32 / G) - 1) / (32 / G);
     const int64_t blocks = (warps + 7) / 8;
-    k_adjoint_lines<T, ADJ_M, G><<<dim3(unsigned(blocks)), 256, 0, st>>>(a, b, c, x, gx, ga, gb,
-                                                                         gc, gd, L.nsys, L.n);
+    // 16-byte vector access needs every array 16-byte aligned and each
+    // system's start on a 16-byte boundary (n a multiple of 16 / sizeof(T))
+    const void *ptrs[9] = {a, b, c, x, gx, ga, gb, gc, gd};
+    int vec_ok = (L.n * int64_t(sizeof(T))) % 16 == 0;
+    for (const void *p : ptrs)
+        if (p && !is_aligned16(p)) vec_ok = 0;
+    k_adjoint_lines<T, ADJ_M, G><<<dim3(unsigned(blocks)), 256, 0, st>>>(
+        a, b, c, x, gx, ga, gb, gc, gd, L.nsys, L.n, vec_ok);
 }
 
 template <typename T, int NT>
