@@ -57,6 +57,11 @@ typedef enum {
 /* Human-readable name of a status code (static storage). */
 const char *trid_status_string(trid_status s);
 
+/* Text of the most recent CUDA runtime error that made a call of this library
+ * return TRID_ERR_CUDA ("none" if there was none).  Static storage; the
+ * record is process-wide and is not cleared by reading it. */
+const char *trid_last_cuda_error(void);
+
 /*
  * Batched solve along one mesh axis (Section 2.1; Algorithm "thomas" of
  * Section 2 defines the result, which is the unique x = A^{-1} d).

@@ -19,6 +19,7 @@
 #include "trid_device.cuh"
 #include "trid_strided.cuh"
 #include "trid_adi_static.cuh"
+#include "trid_adi_2pass.cuh"
 #include "../../include/trid.h"
 #include "trid_internal.h"
 
@@ -262,6 +263,171 @@ static void adi_strided(T lam, const T *d, T *out, int acc, const Lines &L, cuda
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two-pass 3D schedule (trid_adi_2pass.cuh).  Workspace: e (mesh-sized), the
+// reduced y arrays rs / re ([z][tile][x]) and one counter per plane.
+// ---------------------------------------------------------------------------
+struct Adi2Layout {
+    size_t e, red, cnt, tab, total;
+};
+
+static Adi2Layout adi2_layout(const int64_t *n3, size_t esz) {
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    Adi2Layout l;
+    l.e = up(size_t(n3[0] * n3[1] * n3[2]) * esz);
+    l.red = up(size_t(n3[0] * ((n3[1] + ADI_YM - 1) / ADI_YM) * n3[2]) * esz);
+    l.cnt = up(size_t(n3[2]) * sizeof(unsigned));
+    l.tab = up(size_t(AS_NLANE) * 32 * esz);
+    l.total = l.e + 2 * l.red + l.cnt + l.tab;
+    return l;
+}
+
+static bool adi2_eligible(const int64_t *n3, int ndim) {
+    if (ndim != 3) return false;
+    for (int k = 0; k < 3; ++k)
+        if (n3[k] % 16 != 0 || n3[k] < 16 || n3[k] > ADI_MAX_N) return false;
+    if (n3[2] < 32) return false;  // the z pass needs whole warps of consumers
+    return true;
+}
+
+template <typename T>
+static bool adi2_tables(const int64_t *n3, T lam, AdiStatics<T, ADI_XM> &sx,
+                        AdiStatics<T, ADI_YM> &sy, AdiStatics<T, ADI_YM> &sz, YReduced<T> &ry,
+                        YSubst<T> &ys) {
+    double red[4];
+    if (!adi_static_fill<T, ADI_XM>(sx, int(n3[0]), double(lam))) return false;
+    if (!adi_static_fill<T, ADI_YM>(sy, int(n3[1]), double(lam), red)) return false;
+    if (!adi_static_fill<T, ADI_YM>(sz, int(n3[2]), double(lam))) return false;
+    // reduced y system: unknowns (s_0, e_0, s_1, e_1, ...); row s_k couples
+    // e_{k-1} (as) and e_k (cs), row e_k couples s_k (ae) and s_{k+1} (ce);
+    // the first tile's start row and the last tile's end row are identities
+    const int nt = int(n3[1] / ADI_YM);
+    const int n2 = 2 * nt;
+    double sub[32] = {0}, sup[32] = {0};
+    for (int k = 0; k < nt; ++k) {
+        sub[2 * k] = (k > 0) ? red[0] : 0.0;
+        sup[2 * k] = (k > 0) ? red[1] : 0.0;
+        sub[2 * k + 1] = (k < nt - 1) ? red[2] : 0.0;
+        sup[2 * k + 1] = (k < nt - 1) ? red[3] : 0.0;
+    }
+    double cst = 0.0;
+    for (int i = 0; i < 32; ++i) {
+        if (i < n2) {
+            const double wv = 1.0 / (1.0 - sub[i] * cst);
+            cst = sup[i] * wv;
+            ry.sub[i] = T(sub[i]);
+            ry.w[i] = T(wv);
+            ry.cst[i] = T(cst);
+        } else {
+            ry.sub[i] = T(0); ry.w[i] = T(1); ry.cst[i] = T(0);
+        }
+    }
+    ry.n2 = n2;
+    for (int r = 0; r < ADI_YM; ++r) {
+        ys.alpha[r] = (r == 0) ? T(1) : (r == ADI_YM - 1) ? T(0) : -sy.SA[r];
+        ys.beta[r] = (r == 0) ? T(0) : (r == ADI_YM - 1) ? T(1) : -sy.SC[r];
+    }
+    ys.lam = lam;
+    return true;
+}
+
+template <typename T, int G>
+static bool launch_xy(const T *u, T *e, T *rs, T *re, unsigned *cnt, const T *gtab,
+                      const int64_t *n3, T lam, const AdiStatics<T, ADI_XM> &sx,
+                      const AdiStatics<T, ADI_YM> &sy, const YReduced<T> &ry, cudaStream_t st) {
+    const size_t smem = 2 * size_t(ADI_YM) * size_t(n3[0]) * sizeof(T);
+    auto kern = k_adi_xy<T, G>;
+    if (kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), 256, smem) < 1) return false;
+    kern<<<dim3(unsigned(n3[1] / ADI_YM), unsigned(n3[2])), 256, smem, st>>>(
+        u, e, rs, re, cnt, gtab, int(n3[0]), int(n3[1]), int(n3[2]), lam, sx, sy, ry);
+    return launch_ok();
+}
+
+template <typename T, int NT>
+static bool launch_z_ysub(const T *e, const T *rs, const T *re, T *u, const int64_t *n3,
+                          const AdiStatics<T, ADI_YM> &sz, const YSubst<T> &ys, cudaStream_t st) {
+    constexpr int SG = 16;
+    if constexpr ((NT * SG) % 32 != 0) {
+        return false;
+    } else {
+        const DeviceInfo *di = device_info();
+        if (!di) return false;
+        const int64_t nplane = n3[0] * n3[1];
+        const int64_t nred = n3[0] * (n3[1] / ADI_YM);
+        TmaSet maps;
+        if (!encode_lines_map(&maps.map[0], e, int(sizeof(T)), nplane, n3[2], 1, SG) ||
+            !encode_lines_map(&maps.map[1], rs, int(sizeof(T)), nred, n3[2], 1, SG) ||
+            !encode_lines_map(&maps.map[2], re, int(sizeof(T)), nred, n3[2], 1, SG))
+            return false;
+        const size_t slot = (size_t(n3[2]) * SG * sizeof(T) + 127) / 128 * 128;
+        const size_t stage = 3 * slot;
+        const size_t fixed = (4 * NT * (SG + 1) * sizeof(T) + 127) / 128 * 128;
+        auto bytes = [&](int stages) { return size_t(stages) * (stage + 16) + fixed; };
+        const size_t optin = size_t(di->max_smem_optin) - 256;
+        // two blocks per SM with two or more stages (<= 4), else fewer blocks
+        int stages = 0;
+        for (int per = 2; per >= 1 && stages == 0; --per) {
+            size_t cap = size_t(di->smem_per_sm) / per - 4096;
+            if (cap > optin) cap = optin;
+            for (int sg = 4; sg >= 2; --sg)
+                if (bytes(sg) <= cap) { stages = sg; break; }
+        }
+        if (stages == 0) return false;
+        const size_t smem = bytes(stages);
+        auto kern = k_adi_z_ysub<T, NT, SG>;
+        const int per_sm =
+            kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), NT * SG + 32, smem);
+        if (per_sm < 1) return false;
+        const int64_t nbatch = nplane / SG;
+        const int64_t slots = int64_t(di->sm_count) * per_sm;
+        const int64_t grid = nbatch < slots ? nbatch : slots;
+        kern<<<dim3(unsigned(grid)), NT * SG + 32, smem, st>>>(
+            maps, sz, ys, u, int(n3[0]), int(nplane), int(n3[2]), nbatch, stages,
+            device_status_word());
+        return launch_ok();
+    }
+}
+
+template <typename T>
+static trid_status adi_run_2pass(T *u, const int64_t *n3, T lam, int nsteps, char *ws,
+                                 cudaStream_t st) {
+    AdiStatics<T, ADI_XM> sx;
+    AdiStatics<T, ADI_YM> sy, sz;
+    YReduced<T> ry;
+    YSubst<T> ys;
+    if (!adi2_tables<T>(n3, lam, sx, sy, sz, ry, ys)) return TRID_ERR_UNSUPPORTED;
+    const Adi2Layout l = adi2_layout(n3, sizeof(T));
+    T *e = reinterpret_cast<T *>(ws);
+    T *rs = reinterpret_cast<T *>(ws + l.e);
+    T *re = reinterpret_cast<T *>(ws + l.e + l.red);
+    unsigned *cnt = reinterpret_cast<unsigned *>(ws + l.e + 2 * l.red);
+    T *gtab = reinterpret_cast<T *>(ws + l.e + 2 * l.red + l.cnt);
+    k_adi_setup<T><<<1, 256, 0, st>>>(sx, gtab, cnt, int(n3[2]));
+    if (!launch_ok()) return TRID_ERR_CUDA;
+    for (int step = 0; step < nsteps; ++step) {
+        bool ok;
+        switch (sx.ntiles) {
+            case 2: ok = launch_xy<T, 2>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
+            case 4: ok = launch_xy<T, 4>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
+            case 8: ok = launch_xy<T, 8>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
+            case 16: ok = launch_xy<T, 16>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
+            case 32: ok = launch_xy<T, 32>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
+            default: ok = false;
+        }
+        if (!ok) return TRID_ERR_CUDA;
+        switch (sz.ntiles) {
+            case 1: ok = launch_z_ysub<T, 1>(e, rs, re, u, n3, sz, ys, st); break;
+            case 2: ok = launch_z_ysub<T, 2>(e, rs, re, u, n3, sz, ys, st); break;
+            case 4: ok = launch_z_ysub<T, 4>(e, rs, re, u, n3, sz, ys, st); break;
+            case 8: ok = launch_z_ysub<T, 8>(e, rs, re, u, n3, sz, ys, st); break;
+            case 16: ok = launch_z_ysub<T, 16>(e, rs, re, u, n3, sz, ys, st); break;
+            default: ok = false;
+        }
+        if (!ok) return TRID_ERR_CUDA;
+    }
+    return TRID_OK;
+}
+
 template <typename T>
 static trid_status adi_run(T *u, const int64_t *n3, int ndim, T lam, int nsteps, T *w,
                            cudaStream_t st) {
@@ -321,6 +487,7 @@ extern "C" size_t adi_workspace_bytes(const int64_t *dims, int ndim, trid_dtype 
     if (dtype != TRID_F32 && dtype != TRID_F64) return 0;
     if (adi_dims(dims, ndim, n3, total) != TRID_OK) return 0;
     const size_t esz = dtype == TRID_F32 ? 4 : 8;
+    if (ndim == 3) return adi2_layout(n3, esz).total;
     return (size_t(total) * esz + 255) / 256 * 256;
 }
 
@@ -340,10 +507,17 @@ extern "C" trid_status adi_step(void *u, const int64_t *dims, int ndim, double l
     {
         const char *pu = static_cast<const char *>(u), *pw = static_cast<const char *>(workspace);
         const size_t bytes = size_t(total) * esz;
-        if (pu < pw + bytes && pw < pu + bytes) return TRID_ERR_INVALID_ARG;
+        const size_t wbytes = adi_workspace_bytes(dims, ndim, dtype);
+        if (pu < pw + wbytes && pw < pu + bytes) return TRID_ERR_INVALID_ARG;
     }
     if (nsteps == 0) return TRID_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (adi2_eligible(n3, ndim) && is_aligned16(u)) {
+        char *ws = static_cast<char *>(workspace);
+        if (dtype == TRID_F32)
+            return adi_run_2pass<float>(static_cast<float *>(u), n3, float(lambda), nsteps, ws, st);
+        return adi_run_2pass<double>(static_cast<double *>(u), n3, lambda, nsteps, ws, st);
+    }
     if (dtype == TRID_F32)
         return adi_run<float>(static_cast<float *>(u), n3, ndim, float(lambda), nsteps,
                               static_cast<float *>(workspace), st);

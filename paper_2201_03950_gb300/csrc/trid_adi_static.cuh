@@ -41,8 +41,10 @@ struct AdiStatics {
 };
 
 // Host: fill the tables for a line of n nodes (n % M == 0, M <= n <= 32 M).
+// If red4 is given it receives the interior tiles' reduced-row coefficients
+// (as, cs of the start row; ae, ce of the end row) in double precision.
 template <typename T, int AS_M>
-inline bool adi_static_fill(AdiStatics<T, AS_M> &s, int n, double lam) {
+inline bool adi_static_fill(AdiStatics<T, AS_M> &s, int n, double lam, double *red4 = nullptr) {
     if (n % AS_M != 0 || n < AS_M || n > 32 * AS_M) return false;
     int Gt = 1;
     while (Gt * AS_M < n) Gt <<= 1;
@@ -72,6 +74,9 @@ inline bool adi_static_fill(AdiStatics<T, AS_M> &s, int n, double lam) {
     const double rb = 1.0 / (1.0 - c0 * ah[1]);
     const double as_in = a0 * rb, cs_in = -(c0 * ch[1]) * rb;
     const double ae_in = ah[AS_M - 1], ce_in = ch[AS_M - 1];
+    if (red4) {
+        red4[0] = as_in; red4[1] = cs_in; red4[2] = ae_in; red4[3] = ce_in;
+    }
     for (int j = 0; j < AS_M; ++j) {
         s.F[j] = T(F[j]); s.G[j] = T(G[j]); s.B[j] = T(B[j]);
         s.SA[j] = T(j >= 1 && j <= AS_M - 2 ? ah[j] : 0.0);
@@ -212,6 +217,31 @@ __device__ __forceinline__ void static_group_solve(const LaneStatics<T> &L, T ds
     T xprev = __shfl_up_sync(FULL, xe, 1, G);
     if (g == 0) xprev = T(0);
     xs = fma(-L.xcs, xe, fma(-L.xas, xprev, ds));
+}
+
+// As static_group_solve, reading the per-lane factors from the staged table
+// (lane g reads column g: conflict-free) instead of holding them in registers.
+template <typename T, int G>
+__device__ __forceinline__ void static_group_solve_tab(const T (*tab)[32], T ds, T de, int g,
+                                                       T &xs, T &xe) {
+    constexpr unsigned FULL = 0xffffffffu;
+    T nds = __shfl_down_sync(FULL, ds, 1, G);
+    if (g + 1 >= G) nds = T(0);
+    T rd = fma(-tab[2][g], nds, fma(-tab[1][g], ds, tab[0][g] * de));
+#pragma unroll
+    for (int k = 0; k < AS_ROUNDS; ++k) {
+        const int st = 1 << k;
+        if (st >= G) break;
+        T dm = __shfl_up_sync(FULL, rd, st, G);
+        T dp = __shfl_down_sync(FULL, rd, st, G);
+        if (g < st) dm = T(0);
+        if (g + st >= G) dp = T(0);
+        rd = fma(-tab[7 + 3 * k][g], dp, fma(-tab[6 + 3 * k][g], dm, tab[5 + 3 * k][g] * rd));
+    }
+    xe = rd;
+    T xprev = __shfl_up_sync(FULL, xe, 1, G);
+    if (g == 0) xprev = T(0);
+    xs = fma(-tab[4][g], xe, fma(-tab[3][g], xprev, ds));
 }
 
 }  // namespace trid

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "trid_internal.h"
@@ -65,15 +66,25 @@ int kernel_blocks_per_sm(const void *kernel, int threads, size_t smem) {
         if (e.kernel == kernel && e.dev == dev && e.threads == threads && e.smem == smem)
             return e.blocks;
     }
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-        cudaSuccess) {
+    // The attribute is per function: raise it to the largest size this
+    // function is ever queried with, never lower it (a cached smaller query
+    // must not shrink the limit a larger launch relies on).
+    int need = int(smem);
+    for (int i = 0; i < g_nocc; ++i)
+        if (g_occ[i].kernel == kernel && g_occ[i].dev == dev && int(g_occ[i].smem) > need)
+            need = int(g_occ[i].smem);
+    const cudaError_t ae =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    if (ae != cudaSuccess) {
         cudaGetLastError();
+        note_cuda_error(ae);
         return 0;
     }
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem) !=
-        cudaSuccess) {
+    const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem);
+    if (oe != cudaSuccess) {
         cudaGetLastError();
+        note_cuda_error(oe);
         return 0;
     }
     if (g_nocc < kOccCache) g_occ[g_nocc++] = OccEntry{kernel, dev, threads, smem, blocks};
@@ -166,6 +177,23 @@ extern "C" const char *trid_status_string(trid_status s) {
         case TRID_ERR_TIMEOUT: return "TRID_ERR_TIMEOUT";
     }
     return "TRID_ERR_UNKNOWN";
+}
+
+namespace trid {
+static std::atomic<int> g_last_cuda_error{0};
+void note_cuda_error(cudaError_t e) {
+    if (e != cudaSuccess) g_last_cuda_error.store(int(e));
+}
+bool launch_ok() {
+    const cudaError_t e = cudaGetLastError();
+    note_cuda_error(e);
+    return e == cudaSuccess;
+}
+}  // namespace trid
+
+extern "C" const char *trid_last_cuda_error(void) {
+    const int e = trid::g_last_cuda_error.load();
+    return e == 0 ? "none" : cudaGetErrorString(cudaError_t(e));
 }
 
 extern "C" const char *trid_version(void) { return "gb300-trid 0.1 (sm_103a)"; }

@@ -47,4 +47,9 @@ trid_status solve_with_scratch(const void *a, const void *b, const void *c, void
 // trid_get_device_status); kernels that run bounded waits record failures there.
 int *device_status_word();
 
+// Record a failed CUDA runtime call (read back by trid_last_cuda_error).
+void note_cuda_error(cudaError_t e);
+// cudaGetLastError() == cudaSuccess after a launch; a failure is recorded.
+bool launch_ok();
+
 }  // namespace trid

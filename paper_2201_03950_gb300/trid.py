@@ -25,7 +25,10 @@ _lib = None
 class TridError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        msg = f"{what}: {STATUS.get(status, status)}"
+        if status == 4 and _lib is not None:
+            msg += f" ({_lib.trid_last_cuda_error().decode()})"
+        super().__init__(msg)
 
 
 def lib_path() -> str:
@@ -64,6 +67,7 @@ def _bind(L):
         "adi_workspace_bytes": ([P, i32, i32], sz),
         "trid_get_device_status": ([P], i32),
         "trid_status_string": ([i32], ctypes.c_char_p),
+        "trid_last_cuda_error": ([], ctypes.c_char_p),
         "trid_version": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():

@@ -217,7 +217,10 @@ ADI_SMALL = [((9, 7, 6), 0.1, 3), ((40, 36, 33), 0.1, 10), ((64, 64, 64), 0.1, 5
              ((3, 3, 3), 0.1, 2), ((24, 100, 7), 0.15, 3), ((16, 8, 5), 0.1, 2),
              ((256, 256, 3), 0.1, 2), ((32, 250, 9), 0.1, 2), ((8, 3, 4), 0.1, 1),
              ((200, 17, 12), 0.25, 2), ((64, 64, 160), 0.1, 2), ((32, 40, 250), 0.1, 1),
-             ((256, 20, 40), 0.1, 1)]
+             ((256, 20, 40), 0.1, 1),
+             # two-pass 3D schedule (all extents multiples of 16, nz >= 32)
+             ((256, 32, 48), 0.1, 3), ((16, 16, 32), 0.3, 4), ((32, 256, 32), 0.2, 2),
+             ((48, 80, 64), 0.15, 3), ((256, 256, 32), 0.1, 2), ((128, 48, 256), 0.1, 2)]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
@@ -235,6 +238,18 @@ def test_adi_elementwise(dims, lam, steps, dtype):
     u0 = (u0 + np.where(interior, pert, 0.0)).astype(dtype)
     ref = oracle.adi(u0, dims, lam, steps)
     got = run_adi(u0, dims, lam, steps, dtype)
+    assert normwise(got, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("dims", [(64, 48, 32), (40, 36, 33), (48, 32)], ids=str)
+def test_adi_nonzero_boundary(dims, dtype):
+    """Random u everywhere, boundary included: the boundary values must stay
+    fixed and enter the neighbours' stencils exactly as in the oracle."""
+    rng = np.random.default_rng(7)
+    u0 = rng.uniform(-1.0, 1.0, int(np.prod(dims))).astype(dtype)
+    ref = oracle.adi(u0, dims, 0.2, 3)
+    got = run_adi(u0, dims, 0.2, 3, dtype)
     assert normwise(got, ref) <= TOL[dtype]
 
 
