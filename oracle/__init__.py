@@ -17,6 +17,8 @@ passage of arXiv 2201.03950 (cited in the C source):
 * ``adi``           -- ADI heat diffusion step, Algorithm "adi" (Section 4.1)
 * ``solve_varlen``  -- a batch of systems of different lengths
 * ``adjoint``       -- transpose solve and coefficient gradients of one solve
+* ``adi2v``         -- 2D ADI with a diffusivity field kappa (faces: node means)
+* ``adi2v_grad``    -- its loss gradient w.r.t. u_0 and kappa (reverse mode)
 * ``dense_solve``   -- Gaussian elimination with partial pivoting (brute force)
 
 All parity is pinned (tests/test_oracle.py); no function is "parity unpinned".
@@ -67,6 +69,8 @@ def _bind(lib):
         "orc_adi": [P, P, i32, f64, i32],
         "orc_solve_varlen": [P, P, P, P, P, P, i64],
         "orc_adjoint": [i64, P, P, P, P, P, P, P, P, P],
+        "orc_adi2v": [P, P, P, f64, i32],
+        "orc_adi2v_grad": [P, P, P, P, f64, i32, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -193,3 +197,25 @@ def adjoint(a, b, c, x, gx, lib=None):
     _check(lib.orc_adjoint(x.size, _p(a), _p(b), _p(c), _p(x), _p(gx), _p(ga), _p(gb), _p(gc),
                            _p(gd)), "adjoint")
     return ga, gb, gc, gd
+
+
+def adi2v(u, kappa, dims, lam: float, nsteps: int, lib=None) -> np.ndarray:
+    """2D ADI with diffusivity field ``kappa``: u after ``nsteps`` steps."""
+    lib = lib or load()
+    w = _f64(u).reshape(-1).copy()
+    k = _f64(kappa).reshape(-1)
+    _check(lib.orc_adi2v(_p(w), _p(k), _dims_c(dims), float(lam), int(nsteps)), "adi2v")
+    return w
+
+
+def adi2v_grad(u0, kappa, target, dims, lam: float, nsteps: int, lib=None):
+    """Return (loss, g_u0, g_kappa, g_coef) for L = mean((u_T - target)^2);
+    g_coef is [6, n]: summed raw gradients of ax, bx, cx, ay, by, cy."""
+    lib = lib or load()
+    u0, k, tg = (_f64(v).reshape(-1) for v in (u0, kappa, target))
+    gu, gk = np.empty_like(u0), np.empty_like(u0)
+    gc = np.empty((6, u0.size))
+    loss = ctypes.c_double(0.0)
+    _check(lib.orc_adi2v_grad(_p(u0), _p(k), _p(tg), _dims_c(dims), float(lam), int(nsteps),
+                              ctypes.byref(loss), _p(gu), _p(gk), _p(gc)), "adi2v_grad")
+    return loss.value, gu, gk, gc

@@ -428,3 +428,231 @@ int orc_adjoint(int64_t n, const double *a, const double *b, const double *c,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Variable-diffusivity 2D ADI and its gradient.                             */
+/*                                                                          */
+/* The ADI step of Section 4.1 (Algorithm "adi", delta form, Dirichlet      */
+/* boundary) with the constant lambda replaced by lambda * kappa at the cell */
+/* faces.  The paper has no variable-coefficient form; the reading used     */
+/* here: face values are arithmetic means of the two nodes,                 */
+/*   kx_p = (kappa_p + kappa_{p+1}) / 2,  ky_p = (kappa_p + kappa_{p+nx})/2, */
+/* and the x operator of a line has, on rows 0 < i < nx-1,                  */
+/*   a_p = -lambda kx_{p-1},  c_p = -lambda kx_p,  b_p = 1 - a_p - c_p,      */
+/* identity rows at i = 0 and i = nx-1 (y alike, stride nx).  A step is     */
+/*   d_p = -c_p (u_{p+1} - u_p) + a_p (u_p - u_{p-1})    (x part)            */
+/*         -c'_p (u_{p+nx} - u_p) + a'_p (u_p - u_{p-nx}) (y part)           */
+/* at interior points (0 on the boundary), w = X^{-1} d, delta = Y^{-1} w,   */
+/* u <- u + delta.  With kappa = 1 this is orc_adi in 2D.                    */
+/* ------------------------------------------------------------------------ */
+static void v2_coef(const double *kappa, int64_t nx, int64_t ny, double lam,
+                    double *ax, double *bx, double *cx, double *ay, double *by, double *cy)
+{
+    for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+            int64_t p = i + nx * j;
+            if (i == 0 || i == nx - 1) { ax[p] = 0.0; bx[p] = 1.0; cx[p] = 0.0; }
+            else {
+                double kl = 0.5 * (kappa[p - 1] + kappa[p]);
+                double kr = 0.5 * (kappa[p] + kappa[p + 1]);
+                ax[p] = -lam * kl; cx[p] = -lam * kr; bx[p] = 1.0 - ax[p] - cx[p];
+            }
+            if (j == 0 || j == ny - 1) { ay[p] = 0.0; by[p] = 1.0; cy[p] = 0.0; }
+            else {
+                double kl = 0.5 * (kappa[p - nx] + kappa[p]);
+                double kr = 0.5 * (kappa[p] + kappa[p + nx]);
+                ay[p] = -lam * kl; cy[p] = -lam * kr; by[p] = 1.0 - ay[p] - cy[p];
+            }
+        }
+}
+
+static int v2_interior(int64_t i, int64_t j, int64_t nx, int64_t ny)
+{
+    return i > 0 && i < nx - 1 && j > 0 && j < ny - 1;
+}
+
+/* Solve along x (axis 0, stride 1) or y (axis 1, stride nx) on every line. */
+static int v2_solve_lines(int axis, int64_t nx, int64_t ny, const double *a, const double *b,
+                          const double *c, const double *d, double *x)
+{
+    int64_t n = axis == 0 ? nx : ny, nl = axis == 0 ? ny : nx;
+    int64_t st = axis == 0 ? 1 : nx, ls = axis == 0 ? nx : 1;
+    size_t sz = (size_t)n * sizeof(double);
+    double *la = malloc(sz), *lb = malloc(sz), *lc = malloc(sz), *ld = malloc(sz), *lx = malloc(sz);
+    int rc = (la && lb && lc && ld && lx) ? 0 : -1;
+    for (int64_t l = 0; l < nl && rc == 0; ++l)
+        for (int64_t k = 0; k < n; ++k) {
+            int64_t p = l * ls + k * st;
+            la[k] = a[p]; lb[k] = b[p]; lc[k] = c[p]; ld[k] = d[p];
+            if (k == n - 1) {
+                rc = orc_thomas(n, la, lb, lc, ld, lx);
+                for (int64_t q = 0; q < n && rc == 0; ++q) x[l * ls + q * st] = lx[q];
+            }
+        }
+    free(la); free(lb); free(lc); free(ld); free(lx);
+    return rc;
+}
+
+/* One step from u: d, w = X^{-1} d, delta = Y^{-1} w (u is not modified). */
+static int v2_step(const double *u, int64_t nx, int64_t ny, const double *co[6], double *d,
+                   double *w, double *delta)
+{
+    const double *ax = co[0], *bx = co[1], *cx = co[2], *ay = co[3], *by = co[4], *cy = co[5];
+    for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+            int64_t p = i + nx * j;
+            if (!v2_interior(i, j, nx, ny)) { d[p] = 0.0; continue; }
+            d[p] = -cx[p] * (u[p + 1] - u[p]) + ax[p] * (u[p] - u[p - 1])
+                 - cy[p] * (u[p + nx] - u[p]) + ay[p] * (u[p] - u[p - nx]);
+        }
+    int rc = v2_solve_lines(0, nx, ny, ax, bx, cx, d, w);
+    if (rc == 0) rc = v2_solve_lines(1, nx, ny, ay, by, cy, w, delta);
+    return rc;
+}
+
+int orc_adi2v(double *u, const double *kappa, const int64_t *dims, double lam, int nsteps)
+{
+    if (!dims || dims[0] < 1 || dims[1] < 1 || nsteps < 0) return -1;
+    int64_t nx = dims[0], ny = dims[1], n = nx * ny;
+    double *buf = malloc((size_t)n * 9 * sizeof(double));
+    if (!buf) return -1;
+    double *co[6];
+    for (int k = 0; k < 6; ++k) co[k] = buf + (size_t)k * n;
+    double *d = buf + 6 * n, *w = buf + 7 * n, *delta = buf + 8 * n;
+    v2_coef(kappa, nx, ny, lam, co[0], co[1], co[2], co[3], co[4], co[5]);
+    int rc = 0;
+    for (int t = 0; t < nsteps && rc == 0; ++t) {
+        rc = v2_step(u, nx, ny, (const double **)co, d, w, delta);
+        for (int64_t p = 0; p < n && rc == 0; ++p) u[p] += delta[p];
+    }
+    free(buf);
+    return rc;
+}
+
+/* Gradient of L = mean((u_T - target)^2) with respect to u_0 and kappa,    */
+/* by reverse mode over stored states.  Per step, with g = dL/du_{t+1}:      */
+/*   g_w = Y^{-T} g, g_d = X^{-T} g_w (orc_adjoint, which also returns the  */
+/*   coefficient gradients -g_w delta_{p-nx} ... and -g_d w_{p-1} ...);      */
+/*   g_d is zero off the interior (d is fixed to 0 there);                  */
+/*   dL/du_t = g + (transposed stencil of d) g_d;                           */
+/*   the stencil adds g_d (u_p - u_{p-1}) to the gradient of a_p and        */
+/*   g_d (u_p - u_{p+1}) to that of c_p (y alike).                          */
+/* The coefficient gradients summed over the steps (raw, per array, when    */
+/* g_coef is not NULL: ax, bx, cx, ay, by, cy) are then taken to the faces  */
+/* (a_p = -lam kx_{p-1}, c_p = -lam kx_p, b_p = 1 + lam (kx_{p-1} + kx_p))    */
+/* and to the nodes (each face is the mean of its two nodes).                */
+/* ------------------------------------------------------------------------ */
+int orc_adi2v_grad(const double *u0, const double *kappa, const double *target,
+                   const int64_t *dims, double lam, int nsteps, double *loss,
+                   double *g_u0, double *g_kappa, double *g_coef)
+{
+    if (!dims || dims[0] < 1 || dims[1] < 1 || nsteps < 0) return -1;
+    int64_t nx = dims[0], ny = dims[1], n = nx * ny;
+    size_t T = (size_t)nsteps;
+    double *st = malloc((size_t)n * (3 * T + 1) * sizeof(double));
+    double *buf = malloc((size_t)n * 20 * sizeof(double));
+    int64_t lmax = nx > ny ? nx : ny;
+    double *lv = malloc((size_t)lmax * 9 * sizeof(double));
+    if (!st || !buf || !lv) { free(st); free(buf); free(lv); return -1; }
+    double *co[6], *G[6];
+    for (int k = 0; k < 6; ++k) { co[k] = buf + (size_t)k * n; G[k] = buf + (size_t)(6 + k) * n; }
+    double *d = buf + 12 * n, *g = buf + 13 * n, *gw = buf + 14 * n, *gd = buf + 15 * n;
+    double *gu = buf + 16 * n, *gk = buf + 17 * n, *gkx = buf + 18 * n, *gky = buf + 19 * n;
+    v2_coef(kappa, nx, ny, lam, co[0], co[1], co[2], co[3], co[4], co[5]);
+    for (size_t q = 0; q < (size_t)n * 6; ++q) G[0][q] = 0.0;
+    /* forward, keeping u_t, w_t, delta_t */
+    double *U = st, *W = st + (size_t)n * (T + 1), *D = st + (size_t)n * (2 * T + 1);
+    memcpy(U, u0, (size_t)n * sizeof(double));
+    int rc = 0;
+    for (size_t t = 0; t < T && rc == 0; ++t) {
+        rc = v2_step(U + t * n, nx, ny, (const double **)co, d, W + t * n, D + t * n);
+        for (int64_t p = 0; p < n; ++p) U[(t + 1) * n + p] = U[t * n + p] + D[t * n + p];
+    }
+    if (rc) goto out;
+    double L = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+        double r = U[T * n + p] - target[p];
+        L += r * r;
+        g[p] = 2.0 * r / (double)n;
+    }
+    if (loss) *loss = L / (double)n;
+    for (size_t tt = T; tt-- > 0 && rc == 0;) {
+        const double *u = U + tt * n, *w = W + tt * n, *dl = D + tt * n;
+        /* y lines: g_w = Y^{-T} g, coefficient gradients with x = delta */
+        for (int64_t i = 0; i < nx && rc == 0; ++i) {
+            double *la = lv, *lb = lv + lmax, *lc = lv + 2 * lmax, *lx = lv + 3 * lmax;
+            double *lg = lv + 4 * lmax, *oa = lv + 5 * lmax, *ob = lv + 6 * lmax, *oc = lv + 7 * lmax;
+            double *lgd = lv + 8 * lmax;
+            for (int64_t j = 0; j < ny; ++j) {
+                int64_t p = i + nx * j;
+                la[j] = co[3][p]; lb[j] = co[4][p]; lc[j] = co[5][p]; lx[j] = dl[p]; lg[j] = g[p];
+            }
+            rc = orc_adjoint(ny, la, lb, lc, lx, lg, oa, ob, oc, lgd);
+            for (int64_t j = 0; j < ny && rc == 0; ++j) {
+                int64_t p = i + nx * j;
+                G[3][p] += oa[j]; G[4][p] += ob[j]; G[5][p] += oc[j]; gw[p] = lgd[j];
+            }
+        }
+        /* x lines: g_d = X^{-T} g_w, with x = w */
+        for (int64_t j = 0; j < ny && rc == 0; ++j) {
+            double *la = lv, *lb = lv + lmax, *lc = lv + 2 * lmax, *lx = lv + 3 * lmax;
+            double *lg = lv + 4 * lmax, *oa = lv + 5 * lmax, *ob = lv + 6 * lmax, *oc = lv + 7 * lmax;
+            double *lgd = lv + 8 * lmax;
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = i + nx * j;
+                la[i] = co[0][p]; lb[i] = co[1][p]; lc[i] = co[2][p]; lx[i] = w[p]; lg[i] = gw[p];
+            }
+            rc = orc_adjoint(nx, la, lb, lc, lx, lg, oa, ob, oc, lgd);
+            for (int64_t i = 0; i < nx && rc == 0; ++i) {
+                int64_t p = i + nx * j;
+                G[0][p] += oa[i]; G[1][p] += ob[i]; G[2][p] += oc[i]; gd[p] = lgd[i];
+            }
+        }
+        if (rc) break;
+        /* stencil of d: transposed into dL/du_t, and into the a, c gradients */
+        for (int64_t p = 0; p < n; ++p) gu[p] = g[p];
+        for (int64_t j = 1; j < ny - 1; ++j)
+            for (int64_t i = 1; i < nx - 1; ++i) {
+                int64_t p = i + nx * j;
+                double gm = gd[p];
+                gu[p + 1] += -co[2][p] * gm;
+                gu[p - 1] += -co[0][p] * gm;
+                gu[p + nx] += -co[5][p] * gm;
+                gu[p - nx] += -co[3][p] * gm;
+                gu[p] += (co[0][p] + co[2][p] + co[3][p] + co[5][p]) * gm;
+                G[0][p] += gm * (u[p] - u[p - 1]);
+                G[2][p] += gm * (u[p] - u[p + 1]);
+                G[3][p] += gm * (u[p] - u[p - nx]);
+                G[5][p] += gm * (u[p] - u[p + nx]);
+            }
+        for (int64_t p = 0; p < n; ++p) g[p] = gu[p];
+    }
+    if (rc) goto out;
+    memcpy(g_u0, g, (size_t)n * sizeof(double));
+    if (g_coef) memcpy(g_coef, G[0], (size_t)n * 6 * sizeof(double));
+    /* to the faces: gkx[q] is the face between q and q+1 */
+    for (int64_t p = 0; p < n; ++p) { gkx[p] = 0.0; gky[p] = 0.0; gk[p] = 0.0; }
+    for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+            int64_t p = i + nx * j;
+            if (i > 0 && i < nx - 1) {
+                gkx[p - 1] += lam * (G[1][p] - G[0][p]);
+                gkx[p] += lam * (G[1][p] - G[2][p]);
+            }
+            if (j > 0 && j < ny - 1) {
+                gky[p - nx] += lam * (G[4][p] - G[3][p]);
+                gky[p] += lam * (G[4][p] - G[5][p]);
+            }
+        }
+    /* to the nodes */
+    for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+            int64_t p = i + nx * j;
+            if (i < nx - 1) { gk[p] += 0.5 * gkx[p]; gk[p + 1] += 0.5 * gkx[p]; }
+            if (j < ny - 1) { gk[p] += 0.5 * gky[p]; gk[p + nx] += 0.5 * gky[p]; }
+        }
+    memcpy(g_kappa, gk, (size_t)n * sizeof(double));
+out:
+    free(st); free(buf); free(lv);
+    return rc;
+}

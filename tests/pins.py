@@ -11,7 +11,10 @@ Sources of truth used here (none of them re-types an oracle formula):
   * the discrete heat-equation eigenmode decay factor of the ADI step;
   * dense Kronecker-product assembly of one ADI step on a tiny mesh;
   * the transpose identity <A^{-1} d, g> = <d, A^{-T} g> and central finite
-    differences for the adjoint.
+    differences for the adjoint;
+  * for the diffusivity-field ADI: the constant-field case against the
+    constant-coefficient step, a flux-form (D^T K D) dense assembly of the
+    operators, and central finite differences of its loss.
 """
 from __future__ import annotations
 
@@ -325,5 +328,166 @@ def pin_adjoint(lib, tol=1e-7):
     return ok, max(worst_tight, worst_fd)
 
 
+def _flux_ops(kappa, dims, lam):
+    """Dense X, Y operators and the explicit part of one step, assembled in
+    flux form: L_axis = -D^T K D with D the forward difference between
+    neighbouring nodes and K the face diffusivities (mean of the two nodes);
+    boundary rows of X, Y become identity rows and the explicit part is
+    masked to the interior."""
+    nx, ny = dims
+    n = nx * ny
+    idx = lambda i, j: i + nx * j
+    ops = []
+    for axis in (0, 1):
+        faces = []
+        for j in range(ny):
+            for i in range(nx):
+                if (axis == 0 and i < nx - 1) or (axis == 1 and j < ny - 1):
+                    q = idx(i + 1, j) if axis == 0 else idx(i, j + 1)
+                    faces.append((idx(i, j), q))
+        D = np.zeros((len(faces), n))
+        K = np.zeros(len(faces))
+        for f, (p0, p1) in enumerate(faces):
+            D[f, p0], D[f, p1] = -1.0, 1.0
+            K[f] = 0.5 * (kappa[p0] + kappa[p1])
+        L = -(D.T * K) @ D
+        op = np.eye(n) - lam * L
+        for j in range(ny):
+            for i in range(nx):
+                end = (i in (0, nx - 1)) if axis == 0 else (j in (0, ny - 1))
+                if end:
+                    op[idx(i, j), :] = 0.0
+                    op[idx(i, j), idx(i, j)] = 1.0
+        ops.append((op, L))
+    mask = np.zeros(n)
+    for j in range(1, ny - 1):
+        for i in range(1, nx - 1):
+            mask[idx(i, j)] = 1.0
+    E = lam * (ops[0][1] + ops[1][1]) * mask[:, None]
+    return ops[0][0], ops[1][0], E
+
+
+def _flux_adi(u, kappa, dims, lam, steps):
+    X, Y, E = _flux_ops(kappa, dims, lam)
+    for _ in range(steps):
+        u = u + np.linalg.solve(Y, np.linalg.solve(X, E @ u))
+    return u
+
+
+def pin_adi2v(lib, tol=1e-12):
+    """Diffusivity-field 2D ADI: kappa = 1 is the constant-coefficient step;
+    kappa = s with lambda equals kappa = 1 with s lambda; a varying field
+    matches the dense flux-form assembly (LAPACK solves)."""
+    worst = 0.0
+    rng = np.random.default_rng(23)
+    dims = (9, 7)
+    n = 63
+    u0 = rng.uniform(-1, 1, n)
+    ref = oracle.adi(u0, dims, 0.3, 4, lib=lib)
+    worst = max(worst, rel(oracle.adi2v(u0, np.ones(n), dims, 0.3, 4, lib=lib), ref))
+    worst = max(worst, rel(oracle.adi2v(u0, np.full(n, 2.5), dims, 0.12, 4, lib=lib), ref))
+    for dims, steps in (((6, 5), 3), ((4, 8), 2), ((3, 3), 2)):
+        n = dims[0] * dims[1]
+        u0 = rng.uniform(-1, 1, n)
+        kap = rng.uniform(0.3, 2.0, n)
+        got = oracle.adi2v(u0, kap, dims, 0.4, steps, lib=lib)
+        worst = max(worst, rel(got, _flux_adi(u0, kap, dims, 0.4, steps)))
+    return worst <= tol, worst
+
+
+def pin_adi2v_grad(lib, tol=1e-6):
+    """Loss gradient of the diffusivity-field ADI against central finite
+    differences of the dense flux-form forward: every component of g_kappa
+    and g_u0 on a tiny mesh, and the raw coefficient gradients (ax .. cy)
+    against differences of a forward whose six coefficient arrays are
+    perturbed directly."""
+    rng = np.random.default_rng(29)
+    dims, steps, lam = (5, 4), 2, 0.35
+    nx, ny = dims
+    n = nx * ny
+    u0 = rng.uniform(-1, 1, n)
+    kap = rng.uniform(0.4, 1.8, n)
+    tg = rng.uniform(-1, 1, n)
+    loss, gu, gk, gc = oracle.adi2v_grad(u0, kap, tg, dims, lam, steps, lib=lib)
+
+    def L_of(u, k):
+        return float(np.mean((_flux_adi(u, k, dims, lam, steps) - tg) ** 2))
+
+    h = 1e-6
+    worst = abs(loss - L_of(u0, kap)) / abs(loss)
+    scale = max(np.max(np.abs(gu)), np.max(np.abs(gk)))
+    for p in range(n):
+        e = np.zeros(n)
+        e[p] = h
+        fu = (L_of(u0 + e, kap) - L_of(u0 - e, kap)) / (2 * h)
+        fk = (L_of(u0, kap + e) - L_of(u0, kap - e)) / (2 * h)
+        worst = max(worst, abs(fu - gu[p]) / scale, abs(fk - gk[p]) / scale)
+
+    # raw coefficient arrays as independent inputs
+    X0, Y0, E0 = _flux_ops(kap, dims, lam)
+
+    def coef_arrays(op, axis):
+        a, b, c = np.zeros(n), np.zeros(n), np.zeros(n)
+        st = 1 if axis == 0 else nx
+        for j in range(ny):
+            for i in range(nx):
+                p = i + nx * j
+                b[p] = op[p, p]
+                end = (i in (0, nx - 1)) if axis == 0 else (j in (0, ny - 1))
+                if not end:
+                    a[p], c[p] = op[p, p - st], op[p, p + st]
+        return a, b, c
+
+    base = list(coef_arrays(X0, 0)) + list(coef_arrays(Y0, 1))
+
+    def L_coef(arrs):
+        ops = []
+        for axis in (0, 1):
+            a, b, c = arrs[3 * axis: 3 * axis + 3]
+            st = 1 if axis == 0 else nx
+            op = np.zeros((n, n))
+            for j in range(ny):
+                for i in range(nx):
+                    p = i + nx * j
+                    op[p, p] = b[p]
+                    end = (i in (0, nx - 1)) if axis == 0 else (j in (0, ny - 1))
+                    if not end:
+                        op[p, p - st], op[p, p + st] = a[p], c[p]
+            ops.append(op)
+        # explicit part from the off-diagonal coefficients alone (the
+        # diagonal b enters only the implicit operators): at interior p,
+        # d_p = sum over axes of -c_p (u_{p+s} - u_p) + a_p (u_p - u_{p-s})
+        E = np.zeros((n, n))
+        for axis in (0, 1):
+            a, _, c = arrs[3 * axis: 3 * axis + 3]
+            st = 1 if axis == 0 else nx
+            for j in range(1, ny - 1):
+                for i in range(1, nx - 1):
+                    p = i + nx * j
+                    E[p, p - st] -= a[p]
+                    E[p, p + st] -= c[p]
+                    E[p, p] += a[p] + c[p]
+        u = u0.copy()
+        for _ in range(steps):
+            u = u + np.linalg.solve(ops[1], np.linalg.solve(ops[0], E @ u))
+        return float(np.mean((u - tg) ** 2))
+
+    gscale = max(np.max(np.abs(gc)), 1e-30)
+    for k in range(6):
+        for p in rng.choice(n, 6, replace=False):
+            i, j = p % nx, p // nx
+            interior_row = (0 < i < nx - 1) if k < 3 else (0 < j < ny - 1)
+            if k % 3 != 1 and not interior_row:
+                continue  # a, c of an identity row are not part of the operator
+            ap = [v.copy() for v in base]
+            am = [v.copy() for v in base]
+            ap[k][p] += h
+            am[k][p] -= h
+            fd = (L_coef(ap) - L_coef(am)) / (2 * h)
+            worst = max(worst, abs(fd - gc[k][p]) / gscale)
+    return worst <= tol, worst
+
+
 ALL_PINS = [pin_lapack, pin_dense_general, pin_exact_rational, pin_toeplitz, pin_manufactured,
-            pin_mesh, pin_adi_eigenmode, pin_adi_dense, pin_varlen, pin_adjoint]
+            pin_mesh, pin_adi_eigenmode, pin_adi_dense, pin_varlen, pin_adjoint, pin_adi2v,
+            pin_adi2v_grad]

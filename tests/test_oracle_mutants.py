@@ -32,6 +32,16 @@ MUTANTS = [
     ("adjoint_wrong_neighbour", "gc[i] = (i == n - 1) ? 0.0 : -gd[i] * x[i + 1];",
      "gc[i] = (i == n - 1) ? 0.0 : -gd[i] * x[i];"),
     ("dense_no_pivoting", "if (v > best) { best = v; piv = r; }", "if (0) { best = v; piv = r; }"),
+    ("adi2v_face_mean", "double kr = 0.5 * (kappa[p] + kappa[p + 1]);",
+     "double kr = 0.5 * (kappa[p] + kappa[p]);"),
+    ("adi2v_rhs_sign", "d[p] = -cx[p] * (u[p + 1] - u[p]) + ax[p] * (u[p] - u[p - 1])",
+     "d[p] = -cx[p] * (u[p + 1] - u[p]) - ax[p] * (u[p] - u[p - 1])"),
+    ("adi2v_grad_transposed_stencil", "gu[p + 1] += -co[2][p] * gm;", "gu[p + 1] += -co[0][p] * gm;"),
+    ("adi2v_grad_dropped_stencil_term", "G[0][p] += gm * (u[p] - u[p - 1]);", "G[0][p] += 0.0;"),
+    ("adi2v_grad_face", "gkx[p] += lam * (G[1][p] - G[2][p]);", "gkx[p] += lam * (G[1][p] - G[0][p]);"),
+    ("adi2v_grad_loss_scale", "g[p] = 2.0 * r / (double)n;", "g[p] = r / (double)n;"),
+    ("adi2v_grad_wrong_state", "const double *u = U + tt * n, *w = W + tt * n",
+     "const double *u = U + (tt + 1) * n, *w = W + tt * n"),
 ]
 
 
