@@ -177,7 +177,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     names = ["solve_x", "solve_y", "solve_z", "adi_step"]
-    launches_per_step = 3 * 1 + 3  # one kernel per solve; RHS+x, y, z+accumulate per ADI step
+    launches_per_step = 3 * 1 + 3  # one kernel per solve; setup, RHS+x+y tile pass, y substitution+z per ADI step
     nbytes = {"solve_x": metrics.solve_bytes(total, esz), "solve_y": metrics.solve_bytes(total, esz),
               "solve_z": metrics.solve_bytes(total, esz),
               "adi_step": metrics.adi_step_bytes(total, esz)}
@@ -288,6 +288,54 @@ def run_ours(args):
                                "frac": round(gbs / peaks()[0], 4),
                                "ratio_to_forward_GBps": round(gbs / fwd, 3)}
         del tgx, tx, outs
+
+        # differentiable 2D ADI with a diffusivity field: 1024^2 FP32, 50 steps,
+        # checkpoints every 10; forward (17 words per point and step: stencil
+        # 6, x solve 5, y solve into u 6) and backward (65 words per point and
+        # step: segment recompute 21, two adjoint solves 2 x 9, stencil
+        # transpose with the summed coefficient gradients 26)
+        try:
+            dv = (1024, 1024)
+            nv = dv[0] * dv[1]
+            u0v = torch.from_numpy(inputs.target_field(dv, seed=3, dtype=np.float32)).to(dev)
+            kv = torch.from_numpy(inputs.diffusivity_field(dv, seed=0, dtype=np.float32)).to(dev)
+            tv = torch.from_numpy(inputs.target_field(dv, seed=5, dtype=np.float32)).to(dev)
+            stv, ev = 50, 10
+            wsv = torch.empty(trid.adi2v_workspace_bytes(dv, stv, ev, torch.float32),
+                              dtype=torch.uint8, device=dev)
+            ckv = torch.empty(trid.adi2v_checkpoint_bytes(dv, stv, ev, torch.float32),
+                              dtype=torch.uint8, device=dev)
+            uTv = torch.empty_like(u0v)
+            tf, tb = [], []
+            for it in range(4):
+                flush.fill_(it + 9)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                trid.adi2v_forward(u0v, kv, dv, 0.2, stv, ev, uT=uTv, ckpt=ckv, workspace=wsv,
+                                   stream=stream)
+                e1.record(stream)
+                gv2 = 2.0 * (uTv - tv) / nv
+                flush.fill_(it + 10)
+                e1b = torch.cuda.Event(enable_timing=True)
+                e1b.record(stream)
+                trid.adi2v_backward(gv2, kv, dv, 0.2, stv, ev, ckv, workspace=wsv, stream=stream)
+                e2.record(stream)
+                torch.cuda.synchronize()
+                if it:
+                    tf.append(e0.elapsed_time(e1))
+                    tb.append(e1b.elapsed_time(e2))
+            mf, mb = statistics.mean(tf), statistics.mean(tb)
+            bf, bb = 17 * nv * 4 * stv, 65 * nv * 4 * stv
+            uni = nbytes["solve_x"] / (statistics.mean(per["solve_x"]) * 1e-3) / 1e9
+            gf, gbk = bf / (mf * 1e-3) / 1e9, bb / (mb * 1e-3) / 1e9
+            gtot = (bf + bb) / ((mf + mb) * 1e-3) / 1e9
+            secondary["adi2v_1024sq_50steps_ckpt10"] = {
+                "forward_ms": round(mf, 3), "backward_ms": round(mb, 3),
+                "forward_GBps": round(gf, 1), "backward_GBps": round(gbk, 1),
+                "ratio_to_uniform_x_solve": round(gtot / uni, 3)}
+            del u0v, kv, tv, wsv, ckv, uTv
+        except Exception as exc:
+            secondary["adi2v_1024sq_50steps_ckpt10"] = f"unavailable: {exc}"[:200]
 
         # uneven batch: 8192 systems, lengths log-uniform in [16, 16384], FP32,
         # planning + persistent solve captured in one CUDA graph and replayed

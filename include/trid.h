@@ -226,6 +226,43 @@ size_t adi_workspace_bytes(const int64_t *dims, int ndim, trid_dtype dtype);
 trid_status trid_get_device_status(trid_stream_t stream);
 
 /* Library version string (static storage). */
+/*
+ * Differentiable 2D ADI with a diffusivity field (reverse mode of the ADI step
+ * of Section 4.1 with checkpointing; the paper has no variable-coefficient
+ * form).  Mesh dims[0] x dims[1], column-major (x contiguous), both >= 3.
+ * Face diffusivities are node means, kx_p = (kappa_p + kappa_{p+1}) / 2, and
+ * on rows 0 < i < nx-1 the x operator is a_p = -lambda kx_{p-1},
+ * c_p = -lambda kx_p, b_p = 1 - a_p - c_p (identity rows at the line ends; y
+ * alike).  One step: d = explicit part -c_p (u_{p+1} - u_p) + a_p (u_p -
+ * u_{p-1}) + (y terms) on the interior, 0 on the boundary; u += Y^{-1} X^{-1} d.
+ *
+ * adi2v_forward: uT = u0 after nsteps steps (uT may equal u0).  If ckpt is
+ *   not NULL it receives u every `every` steps (u0 first), in slots of
+ *   adi2v_checkpoint_bytes / ceil(nsteps / every) bytes; keep it for the
+ *   backward call.
+ * adi2v_backward: from g_uT = dL/du_T, writes g_u0 = dL/du_0 and
+ *   g_kappa = dL/dkappa, and, if g_coef is not NULL, the gradients with
+ *   respect to the six coefficient arrays (ax, bx, cx, ay, by, cy; 6 packed
+ *   mesh arrays) summed over the steps.  Each segment between checkpoints is
+ *   recomputed forward, then run in reverse with trid_solve_batch_adjoint.
+ * Arrays are device arrays of dims[0] * dims[1] elements of `dtype`; outputs
+ * must not alias inputs.  workspace (256-byte aligned) of at least
+ * adi2v_workspace_bytes(dims, nsteps, every, dtype) bytes, ckpt 256-byte
+ * aligned.  Errors: TRID_ERR_INVALID_ARG (bad dims, nsteps < 0, every < 1,
+ * lambda <= 0, NULL arrays), TRID_ERR_ALLOC (workspace or ckpt too small),
+ * TRID_ERR_MISALIGNED, TRID_ERR_CUDA.  Asynchronous on `stream`.
+ */
+size_t adi2v_workspace_bytes(const int64_t *dims, int nsteps, int every, trid_dtype dtype);
+size_t adi2v_checkpoint_bytes(const int64_t *dims, int nsteps, int every, trid_dtype dtype);
+trid_status adi2v_forward(const void *u0, void *uT, const void *kappa, const int64_t *dims,
+                          double lambda, int nsteps, int every, void *ckpt, size_t ckpt_bytes,
+                          trid_dtype dtype, void *workspace, size_t workspace_bytes,
+                          trid_stream_t stream);
+trid_status adi2v_backward(const void *g_uT, void *g_u0, void *g_kappa, void *g_coef,
+                           const void *kappa, const int64_t *dims, double lambda, int nsteps,
+                           int every, const void *ckpt, size_t ckpt_bytes, trid_dtype dtype,
+                           void *workspace, size_t workspace_bytes, trid_stream_t stream);
+
 const char *trid_version(void);
 
 #ifdef __cplusplus

@@ -74,3 +74,30 @@ def loguniform_lengths(nsys: int, lo: int, hi: int, seed: int = 0):
     u = rng.random(nsys)
     lengths = np.rint(np.exp(math.log(lo) + u * math.log(hi / lo))).astype(np.int64)
     return np.clip(lengths, lo, hi)
+
+
+def diffusivity_field(dims, seed: int = 0, sigma: float = 0.3, passes: int = 3,
+                      dtype=np.float64):
+    """Positive diffusivity field kappa = exp(N(0, sigma^2)) per node, smoothed
+    by ``passes`` passes of a 3x3 box filter (edge nodes replicated), flat in
+    column-major order (x fastest)."""
+    nx, ny = int(dims[0]), int(dims[1])
+    rng = np.random.default_rng(seed)
+    k = np.exp(rng.normal(0.0, sigma, (ny, nx)))
+    for _ in range(passes):
+        p = np.pad(k, 1, mode="edge")
+        k = sum(p[1 + dy: 1 + dy + ny, 1 + dx: 1 + dx + nx]
+                for dy in (-1, 0, 1) for dx in (-1, 0, 1)) / 9.0
+    return k.reshape(-1).astype(dtype)
+
+
+def target_field(dims, seed: int = 0, dtype=np.float64):
+    """Seeded smooth target field: a sum of sine eigenmodes (zero on the
+    boundary) plus small uniform noise on the interior."""
+    rng = np.random.default_rng(seed + 7919)
+    t = sine_field(dims, sine_modes(dims, seed=seed + 1), dtype=np.float64)
+    nx, ny = int(dims[0]), int(dims[1])
+    noise = rng.uniform(-0.05, 0.05, (ny, nx))
+    noise[0, :] = noise[-1, :] = 0.0
+    noise[:, 0] = noise[:, -1] = 0.0
+    return (t + noise.reshape(-1)).astype(dtype)

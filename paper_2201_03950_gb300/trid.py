@@ -65,6 +65,10 @@ def _bind(L):
         "trid_adjoint_workspace_bytes": ([P, i32, i32, i32], sz),
         "adi_step": ([P, P, i32, f64, i32, i32, P, sz, P], i32),
         "adi_workspace_bytes": ([P, i32, i32], sz),
+        "adi2v_workspace_bytes": ([P, i32, i32, i32], sz),
+        "adi2v_checkpoint_bytes": ([P, i32, i32, i32], sz),
+        "adi2v_forward": ([P, P, P, P, f64, i32, i32, P, sz, i32, P, sz, P], i32),
+        "adi2v_backward": ([P, P, P, P, P, P, f64, i32, i32, P, sz, i32, P, sz, P], i32),
         "trid_get_device_status": ([P], i32),
         "trid_status_string": ([i32], ctypes.c_char_p),
         "trid_last_cuda_error": ([], ctypes.c_char_p),
@@ -226,6 +230,76 @@ def adi_step(u, dims, lam: float, nsteps: int, workspace, stream=None):
     if st != 0:
         raise TridError(st, "adi_step")
     return u
+
+
+def _code(dtype) -> int:
+    return TRID_F32 if str(dtype).endswith("float32") else TRID_F64
+
+
+def adi2v_workspace_bytes(dims, nsteps: int, every: int, dtype) -> int:
+    dc, _ = _dims(dims)
+    return int(load().adi2v_workspace_bytes(dc, int(nsteps), int(every), _code(dtype)))
+
+
+def adi2v_checkpoint_bytes(dims, nsteps: int, every: int, dtype) -> int:
+    dc, _ = _dims(dims)
+    return int(load().adi2v_checkpoint_bytes(dc, int(nsteps), int(every), _code(dtype)))
+
+
+def _bytes(t):
+    return t.numel() * t.element_size()
+
+
+def adi2v_forward(u0, kappa, dims, lam: float, nsteps: int, every: int = 10, uT=None,
+                  ckpt=None, workspace=None, stream=None):
+    """2D ADI with diffusivity field ``kappa`` (see include/trid.h): returns
+    (uT, ckpt).  ``ckpt`` (uint8 device tensor) keeps the states the backward
+    call recomputes from; pass ckpt=False to skip keeping them."""
+    import torch
+    n = int(dims[0]) * int(dims[1])
+    _check_tensors((u0, kappa, uT), u0, n)
+    L = load()
+    dc, _ = _dims(dims)
+    code = _dtype(u0)
+    if uT is None:
+        uT = torch.empty_like(u0)
+    if ckpt is None:
+        ckpt = torch.empty(adi2v_checkpoint_bytes(dims, nsteps, every, u0.dtype),
+                           dtype=torch.uint8, device=u0.device)
+    if workspace is None:
+        workspace = torch.empty(adi2v_workspace_bytes(dims, nsteps, every, u0.dtype),
+                                dtype=torch.uint8, device=u0.device)
+    ck = None if ckpt is False else ckpt
+    st = L.adi2v_forward(_ptr(u0), _ptr(uT), _ptr(kappa), dc, float(lam), int(nsteps),
+                         int(every), _ptr(ck), 0 if ck is None else _bytes(ck), code,
+                         _ptr(workspace), _bytes(workspace), _stream(stream))
+    if st != 0:
+        raise TridError(st, "adi2v_forward")
+    return uT, ck
+
+
+def adi2v_backward(g_uT, kappa, dims, lam: float, nsteps: int, every: int, ckpt,
+                   want_coef: bool = False, workspace=None, stream=None):
+    """Returns (g_u0, g_kappa, g_coef) where g_coef is a [6, n] tensor of the
+    summed gradients w.r.t. ax, bx, cx, ay, by, cy (None unless want_coef)."""
+    import torch
+    n = int(dims[0]) * int(dims[1])
+    _check_tensors((g_uT, kappa), g_uT, n)
+    L = load()
+    dc, _ = _dims(dims)
+    code = _dtype(g_uT)
+    g_u0 = torch.empty_like(g_uT)
+    g_k = torch.empty_like(g_uT)
+    g_coef = torch.empty((6, n), dtype=g_uT.dtype, device=g_uT.device) if want_coef else None
+    if workspace is None:
+        workspace = torch.empty(adi2v_workspace_bytes(dims, nsteps, every, g_uT.dtype),
+                                dtype=torch.uint8, device=g_uT.device)
+    st = L.adi2v_backward(_ptr(g_uT), _ptr(g_u0), _ptr(g_k), _ptr(g_coef), _ptr(kappa), dc,
+                          float(lam), int(nsteps), int(every), _ptr(ckpt), _bytes(ckpt), code,
+                          _ptr(workspace), _bytes(workspace), _stream(stream))
+    if st != 0:
+        raise TridError(st, "adi2v_backward")
+    return g_u0, g_k, g_coef
 
 
 def device_status(stream=None) -> int:
