@@ -155,16 +155,17 @@ k_adi_xy(const T *__restrict__ u, T *__restrict__ e, T *__restrict__ rs, T *__re
                 // free) shared tile, row k of 2 * YM rows, then solved there
                 const int n2 = ry.n2;
                 T *yv = sd + c;
-#pragma unroll 1
-                for (int k0 = 0; k0 < n2; k0 += 8) {
+                // all loads in flight at once: one L2 round trip
+                {
+                    T tmp[32];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int k = k0 + q;
-                        if (k < n2) {
-                            const T *src = (k & 1) ? re : rs;
-                            yv[k * nx] = __ldcg(src + rbase + size_t(k >> 1) * nx);
-                        }
+                    for (int k = 0; k < 32; ++k) {
+                        const T *src = (k & 1) ? re : rs;
+                        tmp[k] = (k < n2) ? __ldcg(src + rbase + size_t(k >> 1) * nx) : T(0);
                     }
+#pragma unroll
+                    for (int k = 0; k < 32; ++k)
+                        if (k < n2) yv[k * nx] = tmp[k];
                 }
                 T prev = T(0);
 #pragma unroll 4

@@ -7,18 +7,24 @@
 //
 // On the caller's stream, no host synchronisation:
 //   plan            a memset of the work struct, k_varlen_hist (length
-//                   histogram, ceil log2 buckets) and k_varlen_scatter (order[],
-//                   longest bucket first; systems longer than 248 rows first).
-//   k_varlen_solve  persistent: every block first pulls long systems from one
-//                   atomic counter and solves each with all its threads --
-//                   pass 1 reads the system once and writes the two reduced
-//                   rows of every 8-row tile to shared memory; the reduced
-//                   system (a quarter of the length) is reduced again in
-//                   shared memory until it fits one warp, solved with the warp
-//                   shuffles, and substituted back level by level; pass 2
-//                   re-reads the system (now L2-resident), repeats the tile
-//                   pass and writes x.  Then the block pulls batches of short
-//                   systems (one per warp, lane tiles in registers).
+//                   histogram, ceil log2 buckets with the class boundaries
+//                   below forced onto bucket edges) and k_varlen_scatter
+//                   (meta[]: first row and length, longest bucket first).
+//   k_varlen_solve  persistent; every block takes the classes in turn, each
+//                   from its own atomic counter, longest first:
+//     L   (> 4088 rows)  one system per block, two passes: pass 1 reads the
+//                        system and writes the two reduced rows of every
+//                        8-row tile to shared memory; the reduced system is
+//                        reduced again in shared memory until one warp can
+//                        solve it, and substituted back level by level; pass 2
+//                        re-reads the system (L2-resident), repeats the tile
+//                        pass and writes x.
+//     M2  (<= 4088)      one system per block, one pass: every thread keeps
+//                        its tile in registers through the reduced solve.
+//     M1  (<= 1016)      one system per team of 4 warps (4 teams per block,
+//                        named barriers), one pass, the reduced system (<= 256
+//                        rows) solved by the team's first warp.
+//     S   (<= 248)       one system per warp, lane tiles and shuffles.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,28 +39,39 @@ constexpr int VL_M = 8;               // tile height
 constexpr int VL_SHORT = 32 * VL_M;   // most rows (with alignment padding) one warp solves
 constexpr int VL_SHORT_N = VL_SHORT - VL_M;  // systems up to this length go to one warp
 constexpr int VL_THREADS = 512;       // threads per block of the persistent kernel
+constexpr int VL_TEAM = 128;          // threads of an M1 team
+constexpr int VL_M1_N = VL_TEAM * VL_M - VL_M;      // 1016: longest M1 system
+constexpr int VL_M2_N = VL_THREADS * VL_M - VL_M;   // 4088: longest M2 system
 constexpr int VL_BUCKETS = 40;
 constexpr int VL_PLAN_THREADS = 256;
+// first bucket of each class (buckets are ceil log2 of the length, raised to
+// these edges for lengths above the smaller class's limit)
+constexpr int VL_B_M1 = 9, VL_B_M2 = 11, VL_B_L = 13;
 
 struct VarlenWork {
-    unsigned long long next_long;   // work counters
-    unsigned long long next_short;
+    unsigned long long next_long;   // work counters: class L
+    unsigned long long next_short;  // class S
+    unsigned long long next_m2;     // class M2
+    unsigned long long next_m1;     // class M1
     unsigned long long hist[VL_BUCKETS];    // systems per length bucket
     unsigned long long cursor[VL_BUCKETS];  // scatter cursors (relative to the bucket base)
 };
 
-// Workspace layout: VarlenWork, then order[nsys] (int64).
+// Workspace layout: VarlenWork, then meta[nsys]: (first row, length) of the
+// systems in solve order (int64 pairs).
 inline size_t varlen_ws_bytes(int64_t nsys) {
-    return (sizeof(VarlenWork) + 255) / 256 * 256 + size_t(nsys) * sizeof(int64_t);
+    return (sizeof(VarlenWork) + 255) / 256 * 256 + size_t(nsys) * sizeof(longlong2);
 }
 
-// ceil(log2 n) (0 for n <= 1), with every system longer than VL_SHORT_N in a
-// bucket >= 9 and every shorter one in a bucket <= 8: the descending order puts
-// the long systems (one block each) before the short ones (one warp each).
+// ceil(log2 n) (0 for n <= 1), raised so that each class occupies whole
+// buckets: S <= 8, M1 9..10, M2 11..12, L >= 13 (every length fits its class:
+// 2^8 = 256 > 248, 2^10 = 1024 > 1016, 2^12 = 4096 > 4088).
 __device__ __forceinline__ int len_bucket(int64_t n) {
     if (n <= 1) return 0;
     int b = 64 - __clzll((unsigned long long)(n - 1));
-    if (n > VL_SHORT_N && b < 9) b = 9;
+    if (n > VL_SHORT_N && b < VL_B_M1) b = VL_B_M1;
+    if (n > VL_M1_N && b < VL_B_M2) b = VL_B_M2;
+    if (n > VL_M2_N && b < VL_B_L) b = VL_B_L;
     return b < VL_BUCKETS ? b : VL_BUCKETS - 1;
 }
 
@@ -65,9 +82,10 @@ __device__ __forceinline__ unsigned long long bucket_base(const VarlenWork *w, i
     return base;
 }
 
-__device__ __forceinline__ unsigned long long n_long_of(const VarlenWork *w) {
+// Systems in buckets [lo, hi).
+__device__ __forceinline__ unsigned long long n_in_buckets(const VarlenWork *w, int lo, int hi) {
     unsigned long long s = 0;
-    for (int q = 9; q < VL_BUCKETS; ++q) s += w->hist[q];
+    for (int q = lo; q < hi; ++q) s += w->hist[q];
     return s;
 }
 
@@ -78,7 +96,7 @@ __device__ __forceinline__ bool sys_valid(int64_t s0, int64_t n, int64_t total) 
 
 // Planning, two kernels after a memset of the work struct: per-block length
 // histograms added into the global one, then every block reserves a range of
-// each bucket with one atomic and scatters its systems into order[].
+// each bucket with one atomic and scatters its systems into meta[].
 __device__ __forceinline__ int64_t plan_len(const int64_t *__restrict__ offsets, int64_t k,
                                             int64_t total, int *status, bool flag) {
     const int64_t s0 = offsets[k];
@@ -106,7 +124,7 @@ k_varlen_hist(const int64_t *__restrict__ offsets, int64_t nsys, int64_t total, 
 
 __global__ void __launch_bounds__(VL_PLAN_THREADS)
 k_varlen_scatter(const int64_t *__restrict__ offsets, int64_t nsys, int64_t total,
-                 VarlenWork *work, int64_t *__restrict__ order) {
+                 VarlenWork *work, longlong2 *__restrict__ meta) {
     __shared__ unsigned long long hist[VL_BUCKETS];
     __shared__ unsigned long long start[VL_BUCKETS];
     const int tid = threadIdx.x;
@@ -125,9 +143,16 @@ k_varlen_scatter(const int64_t *__restrict__ offsets, int64_t nsys, int64_t tota
         if (tid < VL_BUCKETS && hist[tid])
             start[tid] = bucket_base(work, tid) + atomicAdd(&work->cursor[tid], hist[tid]);
         __syncthreads();
-        if (b >= 0) order[start[b] + local] = k;
+        if (b >= 0) {
+            const int64_t s0 = offsets[k];
+            meta[start[b] + local] = make_longlong2(s0, offsets[k + 1] - s0);
+        }
         __syncthreads();
     }
+}
+
+__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // ---- shared-memory reduced systems: a level holds R rows (unit diagonal) ---
@@ -269,19 +294,64 @@ __device__ __forceinline__ void store_sys_tile(T *out, int accumulate, int64_t s
     }
 }
 
+// Reduce `lv[0]` (rows R of level 0 already written) level by level until one
+// warp can solve the top level, solve it, and substitute back down to level 0
+// (whose solution is then in lv[0].d).  All threads of the block call it.
+template <typename T>
+__device__ void block_reduced_solve(RLevel<T> *lv, int nlevels) {
+    const int warp = threadIdx.x >> 5;
+    int top = 0;
+    while (lv[top].R > VL_SHORT && top + 1 < nlevels) {
+        lv[top + 1].R = 2 * ((lv[top].R + VL_M - 1) / VL_M);
+        level_reduce<T>(lv[top], lv[top + 1]);
+        __syncthreads();
+        ++top;
+    }
+    if (warp == 0) level_warp_solve<T>(lv[top]);
+    __syncthreads();
+    for (int l = top - 1; l >= 0; --l) {
+        level_substitute<T>(lv[l], lv[l + 1]);
+        __syncthreads();
+    }
+}
+
+// Work items of a class come from one atomic counter.  One helper thread per
+// group (block, team or warp) runs ahead: it takes the next item at the start
+// of the current system, loads its (first row, length) after the first
+// phase, and publishes it before the last, so the counter and meta[] round
+// trips overlap the current system's solve.
+struct VItem {
+    long long item, s0, n;
+};
+
+__device__ __forceinline__ VItem vitem_fetch(unsigned long long *ctr, int64_t limit, int64_t base,
+                                             const longlong2 *__restrict__ meta) {
+    VItem v;
+    v.item = (long long)atomicAdd(ctr, 1ull);
+    v.s0 = 0;
+    v.n = 0;
+    if (v.item < limit) {
+        const longlong2 m = meta[base + v.item];
+        v.s0 = m.x;
+        v.n = m.y;
+    }
+    return v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(VL_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c, const T *d,
-               T *out, int accumulate, const int64_t *__restrict__ offsets, int64_t nsys,
-               int64_t total, int64_t max_len, VarlenWork *work,
-               const int64_t *__restrict__ order, int nlevels, int *status) {
+               T *out, int accumulate, int64_t nsys, int64_t total, int64_t max_len,
+               VarlenWork *work, const longlong2 *__restrict__ meta, int nlevels, int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ long long s_item;
-    // level sizes for the longest admissible system
+    __shared__ VItem s_it[2];
+    __shared__ VItem s_team_it[VL_THREADS / VL_TEAM][2];
+    // level sizes for the longest admissible system (at least an M2 system)
     RLevel<T> lv[8];
     {
         T *p = reinterpret_cast<T *>(smem_raw);
-        int64_t R = 2 * ((max_len + 2 * VL_M - 1) / VL_M);  // includes alignment padding
+        const int64_t ml = max_len > VL_M2_N ? max_len : int64_t(VL_M2_N);
+        int64_t R = 2 * ((ml + 2 * VL_M - 1) / VL_M);  // includes alignment padding
         for (int l = 0; l < nlevels; ++l) {
             lv[l].a = p; lv[l].c = p + R; lv[l].d = p + 2 * R;
             p += 3 * R;
@@ -289,25 +359,26 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         }
     }
     const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const int64_t n_long = int64_t(n_long_of(work));
+    const int lane = tid & 31;
+    const int helper = blockDim.x - 1;
+    const int64_t n_l = int64_t(n_in_buckets(work, VL_B_L, VL_BUCKETS));
+    const int64_t n_m2 = int64_t(n_in_buckets(work, VL_B_M2, VL_B_L));
+    const int64_t n_m1 = int64_t(n_in_buckets(work, VL_B_M1, VL_B_M2));
+    const int64_t n_s = nsys - n_l - n_m2 - n_m1;
 
-    // ---- long systems: one per block
-    for (;;) {
-        if (tid == 0) s_item = (long long)atomicAdd(&work->next_long, 1ull);
-        __syncthreads();
-        const int64_t item = s_item;
-        __syncthreads();
-        if (item >= n_long) break;
-        const int64_t k = order[item];
-        const int64_t s0 = offsets[k];
-        const int64_t n = offsets[k + 1] - s0;
-        if (!sys_valid(s0, n, total) || n > max_len) {
-            if (tid == 0 && status) atomicCAS(status, 0, int(TRID_ERR_INVALID_ARG));
-            continue;
-        }
+    // ---- class L: one system per block, two passes
+    if (tid == helper) s_it[0] = vitem_fetch(&work->next_long, n_l, 0, meta);
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const VItem it = s_it[cur];
+        if (it.item >= n_l) break;
+        unsigned long long nx_item = 0;
+        if (tid == helper) nx_item = atomicAdd(&work->next_long, 1ull);
+        const int64_t s0 = it.s0, n = it.n;
+        const bool ok = sys_valid(s0, n, total) && n <= max_len;
+        if (!ok && tid == 0 && status) atomicCAS(status, 0, int(TRID_ERR_INVALID_ARG));
         const int pad = sys_pad<T>(s0);
-        const int64_t ntiles = (n + pad + VL_M - 1) / VL_M;
+        const int64_t ntiles = ok ? (n + pad + VL_M - 1) / VL_M : 0;
         // pass 1: tile reduction of the system into level 0
         lv[0].R = int(2 * ntiles);
         for (int64_t t = tid; t < ntiles; t += blockDim.x) {
@@ -318,21 +389,11 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             lv[0].a[2 * t] = as; lv[0].c[2 * t] = cs; lv[0].d[2 * t] = ds;
             lv[0].a[2 * t + 1] = ae; lv[0].c[2 * t + 1] = ce; lv[0].d[2 * t + 1] = de;
         }
+        longlong2 nx_meta = make_longlong2(0, 0);
+        if (tid == helper && (long long)nx_item < n_l) nx_meta = meta[nx_item];
         __syncthreads();
-        // reduce in shared memory until one warp can solve the top level
-        int top = 0;
-        while (lv[top].R > VL_SHORT && top + 1 < nlevels) {
-            lv[top + 1].R = 2 * ((lv[top].R + VL_M - 1) / VL_M);
-            level_reduce<T>(lv[top], lv[top + 1]);
-            __syncthreads();
-            ++top;
-        }
-        if (warp == 0) level_warp_solve<T>(lv[top]);
-        __syncthreads();
-        for (int l = top - 1; l >= 0; --l) {
-            level_substitute<T>(lv[l], lv[l + 1]);
-            __syncthreads();
-        }
+        if (ok) block_reduced_solve<T>(lv, nlevels);
+        if (tid == helper) s_it[cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
         // pass 2: recompute every tile and substitute its end values
         for (int64_t t = tid; t < ntiles; t += blockDim.x) {
             T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
@@ -345,31 +406,128 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         __syncthreads();  // level 0 is rewritten by the next system
     }
 
-    // ---- short systems: one per warp
-    const int64_t n_short = nsys - n_long;
-    for (;;) {
-        long long item = 0;
-        if (lane == 0) item = (long long)atomicAdd(&work->next_short, 1ull);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_short) break;
-        const int64_t k = order[n_long + item];
-        const int64_t s0 = offsets[k];
-        const int64_t n = offsets[k + 1] - s0;
-        if (n <= 0 || n > VL_SHORT_N || !sys_valid(s0, n, total)) continue;
+    // ---- class M2: one system per block, the tiles stay in registers
+    if (tid == helper) s_it[0] = vitem_fetch(&work->next_m2, n_m2, n_l, meta);
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const VItem it = s_it[cur];
+        if (it.item >= n_m2) break;
+        unsigned long long nx_item = 0;
+        if (tid == helper) nx_item = atomicAdd(&work->next_m2, 1ull);
+        const int64_t s0 = it.s0, n = it.n;
+        const bool ok = sys_valid(s0, n, total) && n <= VL_M2_N;
+        if (!ok && tid == 0 && status) atomicCAS(status, 0, int(TRID_ERR_INVALID_ARG));
         const int pad = sys_pad<T>(s0);
+        const int ntiles = ok ? int((n + pad + VL_M - 1) / VL_M) : 0;  // <= blockDim.x
+        const bool mine = tid < ntiles;
         T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
-        load_sys_tile<T>(a, b, c, d, s0, n, pad, total, lane, ra, rb, rc, rd);
-        T as, cs, ds, ae, ce, de, xs, xe;
-        tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-        group_solve<T, 32>(as, cs, ds, ae, ce, de, lane, xs, xe);
-        tile_substitute<T, VL_M>(ra, rc, rd, xs, xe);
-        store_sys_tile<T>(out, accumulate, s0, n, pad, total, lane, rd);
+        lv[0].R = 2 * ntiles;
+        if (mine) {
+            load_sys_tile<T>(a, b, c, d, s0, n, pad, total, tid, ra, rb, rc, rd);
+            T as, cs, ds, ae, ce, de;
+            tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
+            lv[0].a[2 * tid] = as; lv[0].c[2 * tid] = cs; lv[0].d[2 * tid] = ds;
+            lv[0].a[2 * tid + 1] = ae; lv[0].c[2 * tid + 1] = ce; lv[0].d[2 * tid + 1] = de;
+        }
+        longlong2 nx_meta = make_longlong2(0, 0);
+        if (tid == helper && (long long)nx_item < n_m2) nx_meta = meta[n_l + nx_item];
+        __syncthreads();
+        if (ok) block_reduced_solve<T>(lv, nlevels);
+        if (tid == helper) s_it[cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
+        if (mine) {
+            tile_substitute<T, VL_M>(ra, rc, rd, lv[0].d[2 * tid], lv[0].d[2 * tid + 1]);
+            store_sys_tile<T>(out, accumulate, s0, n, pad, total, tid, rd);
+        }
+        __syncthreads();
+    }
+
+    // ---- class M1: one system per team of 4 warps, tiles in registers
+    {
+        const int team = tid / VL_TEAM, tt = tid % VL_TEAM;
+        const int bar = 1 + team;  // named barrier of the team (0 is __syncthreads)
+        const int thelper = VL_TEAM - 1;
+        const int64_t base1 = n_l + n_m2;
+        // the team's reduced rows: R <= 2 * VL_TEAM
+        T *tbase = reinterpret_cast<T *>(smem_raw) + size_t(team) * 3 * 2 * VL_TEAM;
+        RLevel<T> tl;
+        tl.a = tbase; tl.c = tbase + 2 * VL_TEAM; tl.d = tbase + 4 * VL_TEAM;
+        if (tt == thelper) s_team_it[team][0] = vitem_fetch(&work->next_m1, n_m1, base1, meta);
+        named_barrier_sync(bar, VL_TEAM);
+        for (int cur = 0;; cur ^= 1) {
+            const VItem it = s_team_it[team][cur];
+            if (it.item >= n_m1) break;
+            unsigned long long nx_item = 0;
+            if (tt == thelper) nx_item = atomicAdd(&work->next_m1, 1ull);
+            const int64_t s0 = it.s0, n = it.n;
+            const bool ok = sys_valid(s0, n, total) && n <= VL_M1_N;
+            if (!ok && tt == 0 && status) atomicCAS(status, 0, int(TRID_ERR_INVALID_ARG));
+            const int pad = sys_pad<T>(s0);
+            const int ntiles = ok ? int((n + pad + VL_M - 1) / VL_M) : 0;  // <= VL_TEAM
+            const bool mine = tt < ntiles;
+            T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
+            tl.R = 2 * ntiles;
+            if (mine) {
+                load_sys_tile<T>(a, b, c, d, s0, n, pad, total, tt, ra, rb, rc, rd);
+                T as, cs, ds, ae, ce, de;
+                tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
+                tl.a[2 * tt] = as; tl.c[2 * tt] = cs; tl.d[2 * tt] = ds;
+                tl.a[2 * tt + 1] = ae; tl.c[2 * tt + 1] = ce; tl.d[2 * tt + 1] = de;
+            }
+            longlong2 nx_meta = make_longlong2(0, 0);
+            if (tt == thelper && (long long)nx_item < n_m1) nx_meta = meta[base1 + nx_item];
+            named_barrier_sync(bar, VL_TEAM);
+            if (ok && tt < 32) level_warp_solve<T>(tl);
+            if (tt == thelper)
+                s_team_it[team][cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
+            named_barrier_sync(bar, VL_TEAM);
+            if (mine) {
+                tile_substitute<T, VL_M>(ra, rc, rd, tl.d[2 * tt], tl.d[2 * tt + 1]);
+                store_sys_tile<T>(out, accumulate, s0, n, pad, total, tt, rd);
+            }
+            named_barrier_sync(bar, VL_TEAM);  // the team's rows are rewritten next
+        }
+    }
+
+    // ---- class S: one system per warp; lane 31 runs ahead
+    {
+        const int64_t base0 = n_l + n_m2 + n_m1;
+        VItem it{0, 0, 0};
+        if (lane == 31) it = vitem_fetch(&work->next_short, n_s, base0, meta);
+        for (;;) {
+            const long long item = __shfl_sync(0xffffffffu, it.item, 31);
+            if (item >= n_s) break;
+            const int64_t s0 = __shfl_sync(0xffffffffu, it.s0, 31);
+            const int64_t n = __shfl_sync(0xffffffffu, it.n, 31);
+            unsigned long long nx_item = 0;
+            if (lane == 31) nx_item = atomicAdd(&work->next_short, 1ull);
+            const bool ok = n > 0 && n <= VL_SHORT_N && sys_valid(s0, n, total);
+            const int pad = sys_pad<T>(s0);
+            T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
+            if (ok) load_sys_tile<T>(a, b, c, d, s0, n, pad, total, lane, ra, rb, rc, rd);
+            if (lane == 31) {
+                it.item = (long long)nx_item;
+                it.s0 = 0;
+                it.n = 0;
+                if ((long long)nx_item < n_s) {
+                    const longlong2 m = meta[base0 + nx_item];
+                    it.s0 = m.x;
+                    it.n = m.y;
+                }
+            }
+            if (!ok) continue;
+            T as, cs, ds, ae, ce, de, xs, xe;
+            tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
+            group_solve<T, 32>(as, cs, ds, ae, ce, de, lane, xs, xe);
+            tile_substitute<T, VL_M>(ra, rc, rd, xs, xe);
+            store_sys_tile<T>(out, accumulate, s0, n, pad, total, lane, rd);
+        }
     }
 }
 
 // Levels and shared-memory bytes for systems up to max_len rows.
 template <typename T>
 static bool varlen_levels(int64_t max_len, int &nlevels, size_t &smem) {
+    if (max_len < VL_M2_N) max_len = VL_M2_N;  // the M2 class uses the same levels
     int64_t R = 2 * ((max_len + 2 * VL_M - 1) / VL_M);
     nlevels = 0;
     size_t rows = 0;
@@ -381,6 +539,8 @@ static bool varlen_levels(int64_t max_len, int &nlevels, size_t &smem) {
         R = 2 * ((R + VL_M - 1) / VL_M);
     }
     smem = rows * sizeof(T);
+    const size_t teams = size_t(VL_THREADS / VL_TEAM) * 3 * 2 * VL_TEAM * sizeof(T);
+    if (smem < teams) smem = teams;
     return true;
 }
 
@@ -395,22 +555,22 @@ static trid_status varlen_run(const T *a, const T *b, const T *c, const T *d, T 
     if (!di) return TRID_ERR_CUDA;
     if (smem > size_t(di->max_smem_optin) - 512) return TRID_ERR_UNSUPPORTED;
     VarlenWork *work = static_cast<VarlenWork *>(ws);
-    int64_t *order =
-        reinterpret_cast<int64_t *>(static_cast<char *>(ws) + (sizeof(VarlenWork) + 255) / 256 * 256);
+    longlong2 *meta = reinterpret_cast<longlong2 *>(static_cast<char *>(ws) +
+                                                    (sizeof(VarlenWork) + 255) / 256 * 256);
     int64_t pblocks = (nsys + VL_PLAN_THREADS - 1) / VL_PLAN_THREADS;
     if (pblocks > 4 * int64_t(di->sm_count)) pblocks = 4 * int64_t(di->sm_count);
     if (cudaMemsetAsync(work, 0, sizeof(VarlenWork), st) != cudaSuccess) return TRID_ERR_CUDA;
     k_varlen_hist<<<dim3(unsigned(pblocks)), VL_PLAN_THREADS, 0, st>>>(offsets, nsys, total, work,
                                                                       device_status_word());
     k_varlen_scatter<<<dim3(unsigned(pblocks)), VL_PLAN_THREADS, 0, st>>>(offsets, nsys, total,
-                                                                         work, order);
+                                                                         work, meta);
     if (cudaGetLastError() != cudaSuccess) return TRID_ERR_CUDA;
     auto kern = k_varlen_solve<T>;
     const int per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), VL_THREADS, smem);
     if (per_sm < 1) return TRID_ERR_UNSUPPORTED;
     int64_t grid = int64_t(di->sm_count) * per_sm;
-    kern<<<dim3(unsigned(grid)), VL_THREADS, smem, st>>>(a, b, c, d, out, acc, offsets, nsys,
-                                                         total, max_len, work, order, nlevels,
+    kern<<<dim3(unsigned(grid)), VL_THREADS, smem, st>>>(a, b, c, d, out, acc, nsys, total,
+                                                         max_len, work, meta, nlevels,
                                                          device_status_word());
     return cudaGetLastError() == cudaSuccess ? TRID_OK : TRID_ERR_CUDA;
 }
