@@ -306,7 +306,7 @@ def run_ours(args):
             ckv = torch.empty(trid.adi2v_checkpoint_bytes(dv, stv, ev, torch.float32),
                               dtype=torch.uint8, device=dev)
             uTv = torch.empty_like(u0v)
-            tf, tb = [], []
+            fwd_t, bwd_t = [], []
             for it in range(4):
                 flush.fill_(it + 9)
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -322,9 +322,9 @@ def run_ours(args):
                 e2.record(stream)
                 torch.cuda.synchronize()
                 if it:
-                    tf.append(e0.elapsed_time(e1))
-                    tb.append(e1b.elapsed_time(e2))
-            mf, mb = statistics.mean(tf), statistics.mean(tb)
+                    fwd_t.append(e0.elapsed_time(e1))
+                    bwd_t.append(e1b.elapsed_time(e2))
+            mf, mb = statistics.mean(fwd_t), statistics.mean(bwd_t)
             bf, bb = 17 * nv * 4 * stv, 65 * nv * 4 * stv
             uni = nbytes["solve_x"] / (statistics.mean(per["solve_x"]) * 1e-3) / 1e9
             gf, gbk = bf / (mf * 1e-3) / 1e9, bb / (mb * 1e-3) / 1e9
@@ -479,6 +479,7 @@ def oracle_step(arrs, dims_s, u_adi, dims_adi):
     """One step of the oracle on (possibly sub-sampled) meshes; returns
     (seconds, algorithmic bytes in the FP32 convention)."""
     import oracle
+    from paper_2201_03950_gb300 import metrics
     a, b, c, d = arrs
     t0 = time.perf_counter()
     nb = 0
