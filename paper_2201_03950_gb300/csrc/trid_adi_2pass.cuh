@@ -151,34 +151,31 @@ k_adi_xy(const T *__restrict__ u, T *__restrict__ e, T *__restrict__ rs, T *__re
         __syncthreads();
         if (s_last) {
             if (c < nx) {
-                // the column's reduced right-hand sides are staged in the (now
-                // free) shared tile, row k of 2 * YM rows, then solved there
+                // the column's reduced system, in registers: all loads in
+                // flight at once (one L2 round trip), then the Thomas sweeps
                 const int n2 = ry.n2;
-                T *yv = sd + c;
-                // all loads in flight at once: one L2 round trip
-                {
-                    T tmp[32];
+                T y[32];
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const T *src = (k & 1) ? re : rs;
-                        tmp[k] = (k < n2) ? __ldcg(src + rbase + size_t(k >> 1) * nx) : T(0);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 32; ++k)
-                        if (k < n2) yv[k * nx] = tmp[k];
+                for (int k = 0; k < 32; ++k) {
+                    const T *src = (k & 1) ? re : rs;
+                    y[k] = (k < n2) ? __ldcg(src + rbase + size_t(k >> 1) * nx) : T(0);
                 }
                 T prev = T(0);
-#pragma unroll 4
-                for (int k = 0; k < n2; ++k) {
-                    prev = (yv[k * nx] - ry.sub[k] * prev) * ry.w[k];
-                    yv[k * nx] = prev;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    if (k < n2) {
+                        prev = (y[k] - ry.sub[k] * prev) * ry.w[k];
+                        y[k] = prev;
+                    }
                 }
                 T xn = T(0);
-#pragma unroll 4
-                for (int k = n2 - 1; k >= 0; --k) {
-                    xn = fma(-ry.cst[k], xn, yv[k * nx]);
-                    T *dst = (k & 1) ? re : rs;
-                    dst[rbase + size_t(k >> 1) * nx] = xn;
+#pragma unroll
+                for (int k = 31; k >= 0; --k) {
+                    if (k < n2) {
+                        xn = fma(-ry.cst[k], xn, y[k]);
+                        T *dst = (k & 1) ? re : rs;
+                        dst[rbase + size_t(k >> 1) * nx] = xn;
+                    }
                 }
             }
             if (tid == 0) cnt[z] = 0u;  // ready for the next step
