@@ -227,6 +227,27 @@ trid_status trid_get_device_status(trid_stream_t stream);
 
 /* Library version string (static storage). */
 /*
+ * ADI steps on a batch of meshes (Section 4.1, Algorithm "adi"; the batched
+ * 2D / 3D workloads of Section 4).  u holds nbatch meshes of dims[0] x ...
+ * x dims[ndim-1] points (ndim 2 or 3, every extent 3..256), mesh b starting
+ * at element b * (product of dims), each column-major (x contiguous); every
+ * mesh advances by nsteps steps exactly as with adi_step.  When a mesh and its
+ * right-hand side fit one block's shared memory, all nsteps steps run in one
+ * kernel with the mesh resident on chip (read and written once per call);
+ * otherwise 3D meshes whose extents suit the two-pass 3D schedule (all
+ * multiples of 16, z >= 32) run stacked along z through its kernels, and the
+ * rest go through adi_step one after another.  `workspace` (256-byte
+ * aligned) must hold adi_batched_workspace_bytes(nbatch, dims, ndim, dtype)
+ * bytes (0 in the resident case, where workspace may be NULL).  Errors as
+ * adi_step; asynchronous on `stream`.
+ */
+size_t adi_batched_workspace_bytes(int64_t nbatch, const int64_t *dims, int ndim,
+                                   trid_dtype dtype);
+trid_status adi_step_batched(void *u, int64_t nbatch, const int64_t *dims, int ndim,
+                             double lambda, int nsteps, trid_dtype dtype, void *workspace,
+                             size_t workspace_bytes, trid_stream_t stream);
+
+/*
  * Differentiable 2D ADI with a diffusivity field (reverse mode of the ADI step
  * of Section 4.1 with checkpointing; the paper has no variable-coefficient
  * form).  Mesh dims[0] x dims[1], column-major (x contiguous), both >= 3.

@@ -271,12 +271,12 @@ struct Adi2Layout {
     size_t e, red, cnt, tab, total;
 };
 
-static Adi2Layout adi2_layout(const int64_t *n3, size_t esz) {
+static Adi2Layout adi2_layout(const int64_t *n3, size_t esz, int64_t nb = 1) {
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
     Adi2Layout l;
-    l.e = up(size_t(n3[0] * n3[1] * n3[2]) * esz);
-    l.red = up(size_t(n3[0] * ((n3[1] + ADI_YM - 1) / ADI_YM) * n3[2]) * esz);
-    l.cnt = up(size_t(n3[2]) * sizeof(unsigned));
+    l.e = up(size_t(n3[0] * n3[1] * n3[2]) * esz * size_t(nb));
+    l.red = up(size_t(n3[0] * ((n3[1] + ADI_YM - 1) / ADI_YM) * n3[2]) * esz * size_t(nb));
+    l.cnt = up(size_t(n3[2]) * sizeof(unsigned) * size_t(nb));
     l.tab = up(size_t(AS_NLANE) * 32 * esz);
     l.total = l.e + 2 * l.red + l.cnt + l.tab;
     return l;
@@ -333,19 +333,21 @@ static bool adi2_tables(const int64_t *n3, T lam, AdiStatics<T, ADI_XM> &sx,
 
 template <typename T, int G>
 static bool launch_xy(const T *u, T *e, T *rs, T *re, unsigned *cnt, const T *gtab,
-                      const int64_t *n3, T lam, const AdiStatics<T, ADI_XM> &sx,
+                      const int64_t *n3, int64_t nb, T lam, const AdiStatics<T, ADI_XM> &sx,
                       const AdiStatics<T, ADI_YM> &sy, const YReduced<T> &ry, cudaStream_t st) {
     const size_t smem = 2 * size_t(ADI_YM) * size_t(n3[0]) * sizeof(T);
     auto kern = k_adi_xy<T, G>;
     if (kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), 256, smem) < 1) return false;
-    kern<<<dim3(unsigned(n3[1] / ADI_YM), unsigned(n3[2])), 256, smem, st>>>(
+    if (n3[2] * nb > 65535) return false;
+    kern<<<dim3(unsigned(n3[1] / ADI_YM), unsigned(n3[2] * nb)), 256, smem, st>>>(
         u, e, rs, re, cnt, gtab, int(n3[0]), int(n3[1]), int(n3[2]), lam, sx, sy, ry);
     return launch_ok();
 }
 
 template <typename T, int NT>
 static bool launch_z_ysub(const T *e, const T *rs, const T *re, T *u, const int64_t *n3,
-                          const AdiStatics<T, ADI_YM> &sz, const YSubst<T> &ys, cudaStream_t st) {
+                          int64_t nb, const AdiStatics<T, ADI_YM> &sz, const YSubst<T> &ys,
+                          cudaStream_t st) {
     constexpr int SG = 16;
     if constexpr ((NT * SG) % 32 != 0) {
         return false;
@@ -355,9 +357,9 @@ static bool launch_z_ysub(const T *e, const T *rs, const T *re, T *u, const int6
         const int64_t nplane = n3[0] * n3[1];
         const int64_t nred = n3[0] * (n3[1] / ADI_YM);
         TmaSet maps;
-        if (!encode_lines_map(&maps.map[0], e, int(sizeof(T)), nplane, n3[2], 1, SG) ||
-            !encode_lines_map(&maps.map[1], rs, int(sizeof(T)), nred, n3[2], 1, SG) ||
-            !encode_lines_map(&maps.map[2], re, int(sizeof(T)), nred, n3[2], 1, SG))
+        if (!encode_lines_map(&maps.map[0], e, int(sizeof(T)), nplane, n3[2], nb, SG) ||
+            !encode_lines_map(&maps.map[1], rs, int(sizeof(T)), nred, n3[2], nb, SG) ||
+            !encode_lines_map(&maps.map[2], re, int(sizeof(T)), nred, n3[2], nb, SG))
             return false;
         const size_t slot = (size_t(n3[2]) * SG * sizeof(T) + 127) / 128 * 128;
         const size_t stage = 3 * slot;
@@ -378,7 +380,7 @@ static bool launch_z_ysub(const T *e, const T *rs, const T *re, T *u, const int6
         const int per_sm =
             kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), NT * SG + 32, smem);
         if (per_sm < 1) return false;
-        const int64_t nbatch = nplane / SG;
+        const int64_t nbatch = nplane / SG * nb;
         const int64_t slots = int64_t(di->sm_count) * per_sm;
         const int64_t grid = nbatch < slots ? nbatch : slots;
         kern<<<dim3(unsigned(grid)), NT * SG + 32, smem, st>>>(
@@ -390,37 +392,37 @@ static bool launch_z_ysub(const T *e, const T *rs, const T *re, T *u, const int6
 
 template <typename T>
 static trid_status adi_run_2pass(T *u, const int64_t *n3, T lam, int nsteps, char *ws,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int64_t nb = 1) {
     AdiStatics<T, ADI_XM> sx;
     AdiStatics<T, ADI_YM> sy, sz;
     YReduced<T> ry;
     YSubst<T> ys;
     if (!adi2_tables<T>(n3, lam, sx, sy, sz, ry, ys)) return TRID_ERR_UNSUPPORTED;
-    const Adi2Layout l = adi2_layout(n3, sizeof(T));
+    const Adi2Layout l = adi2_layout(n3, sizeof(T), nb);
     T *e = reinterpret_cast<T *>(ws);
     T *rs = reinterpret_cast<T *>(ws + l.e);
     T *re = reinterpret_cast<T *>(ws + l.e + l.red);
     unsigned *cnt = reinterpret_cast<unsigned *>(ws + l.e + 2 * l.red);
     T *gtab = reinterpret_cast<T *>(ws + l.e + 2 * l.red + l.cnt);
-    k_adi_setup<T><<<1, 256, 0, st>>>(sx, gtab, cnt, int(n3[2]));
+    k_adi_setup<T><<<1, 256, 0, st>>>(sx, gtab, cnt, int(n3[2] * nb));
     if (!launch_ok()) return TRID_ERR_CUDA;
     for (int step = 0; step < nsteps; ++step) {
         bool ok;
         switch (sx.ntiles) {
-            case 2: ok = launch_xy<T, 2>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
-            case 4: ok = launch_xy<T, 4>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
-            case 8: ok = launch_xy<T, 8>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
-            case 16: ok = launch_xy<T, 16>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
-            case 32: ok = launch_xy<T, 32>(u, e, rs, re, cnt, gtab, n3, lam, sx, sy, ry, st); break;
+            case 2: ok = launch_xy<T, 2>(u, e, rs, re, cnt, gtab, n3, nb, lam, sx, sy, ry, st); break;
+            case 4: ok = launch_xy<T, 4>(u, e, rs, re, cnt, gtab, n3, nb, lam, sx, sy, ry, st); break;
+            case 8: ok = launch_xy<T, 8>(u, e, rs, re, cnt, gtab, n3, nb, lam, sx, sy, ry, st); break;
+            case 16: ok = launch_xy<T, 16>(u, e, rs, re, cnt, gtab, n3, nb, lam, sx, sy, ry, st); break;
+            case 32: ok = launch_xy<T, 32>(u, e, rs, re, cnt, gtab, n3, nb, lam, sx, sy, ry, st); break;
             default: ok = false;
         }
         if (!ok) return TRID_ERR_CUDA;
         switch (sz.ntiles) {
-            case 1: ok = launch_z_ysub<T, 1>(e, rs, re, u, n3, sz, ys, st); break;
-            case 2: ok = launch_z_ysub<T, 2>(e, rs, re, u, n3, sz, ys, st); break;
-            case 4: ok = launch_z_ysub<T, 4>(e, rs, re, u, n3, sz, ys, st); break;
-            case 8: ok = launch_z_ysub<T, 8>(e, rs, re, u, n3, sz, ys, st); break;
-            case 16: ok = launch_z_ysub<T, 16>(e, rs, re, u, n3, sz, ys, st); break;
+            case 1: ok = launch_z_ysub<T, 1>(e, rs, re, u, n3, nb, sz, ys, st); break;
+            case 2: ok = launch_z_ysub<T, 2>(e, rs, re, u, n3, nb, sz, ys, st); break;
+            case 4: ok = launch_z_ysub<T, 4>(e, rs, re, u, n3, nb, sz, ys, st); break;
+            case 8: ok = launch_z_ysub<T, 8>(e, rs, re, u, n3, nb, sz, ys, st); break;
+            case 16: ok = launch_z_ysub<T, 16>(e, rs, re, u, n3, nb, sz, ys, st); break;
             default: ok = false;
         }
         if (!ok) return TRID_ERR_CUDA;
@@ -476,6 +478,27 @@ static trid_status adi_dims(const int64_t *dims, int ndim, int64_t (&n3)[3], int
         total *= dims[k];
     }
     return TRID_OK;
+}
+
+// Batches of 3D meshes stacked along z (each mesh keeps its own boundary
+// planes), through the two-pass schedule; used by adi_step_batched.
+bool adi3_batch_eligible(const int64_t *n3, int ndim) { return adi2_eligible(n3, ndim); }
+
+size_t adi3_batch_ws_bytes(const int64_t *n3, size_t esz, int64_t nb) {
+    return adi2_layout(n3, esz, nb).total;
+}
+
+trid_status adi3_batch_run(void *u, int64_t nb, const int64_t *n3, double lam, int nsteps,
+                           trid_dtype dtype, void *ws, size_t ws_bytes, cudaStream_t st) {
+    const size_t esz = dtype == TRID_F32 ? 4 : 8;
+    if (!ws || ws_bytes < adi3_batch_ws_bytes(n3, esz, nb)) return TRID_ERR_ALLOC;
+    if ((reinterpret_cast<uintptr_t>(ws) % 256) != 0) return TRID_ERR_MISALIGNED;
+    if (!is_aligned16(u)) return TRID_ERR_MISALIGNED;
+    if (dtype == TRID_F32)
+        return adi_run_2pass<float>(static_cast<float *>(u), n3, float(lam), nsteps,
+                                    static_cast<char *>(ws), st, nb);
+    return adi_run_2pass<double>(static_cast<double *>(u), n3, lam, nsteps,
+                                 static_cast<char *>(ws), st, nb);
 }
 
 }  // namespace trid

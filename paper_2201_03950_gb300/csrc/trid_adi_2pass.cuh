@@ -70,8 +70,11 @@ k_adi_xy(const T *__restrict__ u, T *__restrict__ e, T *__restrict__ rs, T *__re
     constexpr int PASSES = (YM * G + 255) / 256;
     const int c = tid;  // column of the y tile pass
     {
+        // z: plane over the whole batch (meshes stacked along z); the
+        // boundary test uses the plane's index inside its own mesh
         const int t = int(blockIdx.x), z = int(blockIdx.y);
-        const bool zint = z > 0 && z < nz - 1;
+        const int zl = z % nz;
+        const bool zint = zl > 0 && zl < nz - 1;
         const T *ut = u + size_t(z) * size_t(plane) + size_t(t) * YM * nx;
 
         // x solve of the tile's rows; G lanes per row
@@ -208,6 +211,9 @@ k_adi_z_ysub(const __grid_constant__ TmaSet maps,
              const __grid_constant__ AdiStatics<T, ADI_YM> st,
              const __grid_constant__ YSubst<T> ys, T *out, int nx, int nplane, int n,
              int64_t nbatch, int stages, int *status) {
+    // batches: nbox boxes of SG columns per z line set of one mesh, meshes
+    // stacked (nbatch = nbox * number of meshes)
+    const int64_t nbox = nplane / SG;
     constexpr int M = ADI_YM;
     constexpr int P = SG + 1;
     constexpr int NCONS = NT * SG;
@@ -249,13 +255,14 @@ k_adi_z_ysub(const __grid_constant__ TmaSet maps,
                     break;
                 }
                 mbar_expect_tx(&full[s], tx);
-                const int f0 = int(bt * SG);
+                const int mesh = int(bt / nbox);
+                const int f0 = int(bt - int64_t(mesh) * nbox) * SG;
                 const int y = f0 / nx;
                 const int rx = (y / M) * nx + (f0 - y * nx);
                 unsigned char *dst = smem + s * stage_bytes;
-                tma_load_3d(dst, &maps.map[0], f0, 0, 0, &full[s]);
-                tma_load_3d(dst + slot_bytes, &maps.map[1], rx, 0, 0, &full[s]);
-                tma_load_3d(dst + 2 * slot_bytes, &maps.map[2], rx, 0, 0, &full[s]);
+                tma_load_3d(dst, &maps.map[0], f0, 0, mesh, &full[s]);
+                tma_load_3d(dst + slot_bytes, &maps.map[1], rx, 0, mesh, &full[s]);
+                tma_load_3d(dst + 2 * slot_bytes, &maps.map[2], rx, 0, mesh, &full[s]);
             }
         }
         return;
@@ -284,7 +291,8 @@ k_adi_z_ysub(const __grid_constant__ TmaSet maps,
         const T *se = reinterpret_cast<const T *>(smem + s * stage_bytes);
         const T *sxs = reinterpret_cast<const T *>(smem + s * stage_bytes + slot_bytes);
         const T *sxe = reinterpret_cast<const T *>(smem + s * stage_bytes + 2 * slot_bytes);
-        const int f0 = int(bt * SG);
+        const int mesh = int(bt / nbox);
+        const int f0 = int(bt - int64_t(mesh) * nbox) * SG;
         const int r = (f0 / nx) % M;
         const T al = ys.alpha[r], be = ys.beta[r];
         T d[M];
@@ -317,7 +325,7 @@ k_adi_z_ysub(const __grid_constant__ TmaSet maps,
         if (first) d[0] = b0;
         if (last) d[M - 1] = b1;
         if (ok) {
-            T *ob = out + (f0 + sl);
+            T *ob = out + (size_t(mesh) * n * nplane + f0 + sl);
 #pragma unroll
             for (int j = 0; j < M; ++j)
                 if (i0 + j < n) ob[size_t(i0 + j) * nplane] = d[j];

@@ -47,6 +47,12 @@ trid_status solve_with_scratch(const void *a, const void *b, const void *c, void
 // trid_get_device_status); kernels that run bounded waits record failures there.
 int *device_status_word();
 
+// 3D ADI on a batch of meshes stacked along z (two-pass schedule).
+bool adi3_batch_eligible(const int64_t *n3, int ndim);
+size_t adi3_batch_ws_bytes(const int64_t *n3, size_t esz, int64_t nb);
+trid_status adi3_batch_run(void *u, int64_t nb, const int64_t *n3, double lam, int nsteps,
+                           trid_dtype dtype, void *ws, size_t ws_bytes, cudaStream_t st);
+
 // Record a failed CUDA runtime call (read back by trid_last_cuda_error).
 void note_cuda_error(cudaError_t e);
 // cudaGetLastError() == cudaSuccess after a launch; a failure is recorded.

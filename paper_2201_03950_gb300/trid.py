@@ -65,6 +65,8 @@ def _bind(L):
         "trid_adjoint_workspace_bytes": ([P, i32, i32, i32], sz),
         "adi_step": ([P, P, i32, f64, i32, i32, P, sz, P], i32),
         "adi_workspace_bytes": ([P, i32, i32], sz),
+        "adi_batched_workspace_bytes": ([i64, P, i32, i32], sz),
+        "adi_step_batched": ([P, i64, P, i32, f64, i32, i32, P, sz, P], i32),
         "adi2v_workspace_bytes": ([P, i32, i32, i32], sz),
         "adi2v_checkpoint_bytes": ([P, i32, i32, i32], sz),
         "adi2v_forward": ([P, P, P, P, f64, i32, i32, P, sz, i32, P, sz, P], i32),
@@ -229,6 +231,28 @@ def adi_step(u, dims, lam: float, nsteps: int, workspace, stream=None):
                     workspace.numel() * workspace.element_size(), _stream(stream))
     if st != 0:
         raise TridError(st, "adi_step")
+    return u
+
+
+def adi_step_batched(u, nbatch: int, dims, lam: float, nsteps: int, workspace=None,
+                     stream=None):
+    """Advance each of the ``nbatch`` meshes stored back to back in ``u`` by
+    ``nsteps`` ADI steps (see include/trid.h)."""
+    import torch
+    per = 1
+    for v in dims:
+        per *= int(v)
+    _check_tensors((u,), u, per * int(nbatch))
+    L = load()
+    dc, nd = _dims(dims)
+    need = int(L.adi_batched_workspace_bytes(int(nbatch), dc, nd, _dtype(u)))
+    if workspace is None and need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=u.device)
+    st = L.adi_step_batched(_ptr(u), int(nbatch), dc, nd, float(lam), int(nsteps), _dtype(u),
+                            _ptr(workspace), 0 if workspace is None else _bytes(workspace),
+                            _stream(stream))
+    if st != 0:
+        raise TridError(st, "adi_step_batched")
     return u
 
 
