@@ -227,6 +227,41 @@ trid_status trid_get_device_status(trid_stream_t stream);
 
 /* Library version string (static storage). */
 /*
+ * Length classes of trid_solve_batch_varlen: systems of up to 248 rows are
+ * solved by one warp each, up to team_max rows by a team of 4 warps, up to
+ * block_max rows by a whole block in one pass, and longer ones by a block in
+ * two passes.  team_max is 248 (no team class), 504 or 1016; block_max is
+ * team_max (no one-pass block class) or one of 1016, 2040, 4088 not below
+ * team_max.  Defaults (trid_solve_batch_varlen): team_max 1016, block_max
+ * 4088.  Not a construct of the paper (its FPGA batches are uniform).
+ */
+typedef struct {
+    int32_t team_max;
+    int32_t block_max;
+} trid_varlen_config;
+
+/* trid_solve_batch_varlen with explicit length classes (cfg == NULL: the
+ * defaults); TRID_ERR_INVALID_ARG for a configuration outside the list above. */
+trid_status trid_solve_batch_varlen_cfg(const void *a, const void *b, const void *c, void *d,
+                                        void *u, const int64_t *offsets, int64_t nsys,
+                                        int64_t total, int64_t max_len, trid_dtype dtype,
+                                        void *workspace, size_t workspace_bytes,
+                                        trid_stream_t stream, const trid_varlen_config *cfg);
+
+/* Autotuner: solves the caller's batch once per admissible configuration (on
+ * a scratch copy of d inside `workspace`; a, b, c, d are not modified), times
+ * each with CUDA events on `stream` (best of three after one warm-up run) and
+ * writes the fastest to *best (and its time in ms to *best_ms if not NULL).
+ * Synchronises `stream`.  workspace: trid_varlen_autotune_workspace_bytes
+ * bytes, 256-byte aligned.  Errors as trid_solve_batch_varlen. */
+size_t trid_varlen_autotune_workspace_bytes(int64_t nsys, int64_t total, trid_dtype dtype);
+trid_status trid_varlen_autotune(const void *a, const void *b, const void *c, const void *d,
+                                 const int64_t *offsets, int64_t nsys, int64_t total,
+                                 int64_t max_len, trid_dtype dtype, void *workspace,
+                                 size_t workspace_bytes, trid_stream_t stream,
+                                 trid_varlen_config *best, float *best_ms);
+
+/*
  * ADI steps on a batch of meshes (Section 4.1, Algorithm "adi"; the batched
  * 2D / 3D workloads of Section 4).  u holds nbatch meshes of dims[0] x ...
  * x dims[ndim-1] points (ndim 2 or 3, every extent 3..256), mesh b starting

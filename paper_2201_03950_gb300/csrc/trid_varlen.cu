@@ -44,9 +44,17 @@ constexpr int VL_M1_N = VL_TEAM * VL_M - VL_M;      // 1016: longest M1 system
 constexpr int VL_M2_N = VL_THREADS * VL_M - VL_M;   // 4088: longest M2 system
 constexpr int VL_BUCKETS = 40;
 constexpr int VL_PLAN_THREADS = 256;
-// first bucket of each class (buckets are ceil log2 of the length, raised to
-// these edges for lengths above the smaller class's limit)
-constexpr int VL_B_M1 = 9, VL_B_M2 = 11, VL_B_L = 13;
+// Buckets are ceil log2 of the length, raised to the class edges for lengths
+// above the smaller class's limit.  The first M1 bucket is fixed; the first M2
+// and L buckets (e1, e2) are run-time choices (trid_varlen_config, picked by
+// trid_varlen_autotune): a class spanning buckets [lo, hi) holds lengths up to
+// 2^(hi-1) - 8, the padding of a 16-byte-aligned tile start included.
+constexpr int VL_B_M1 = 9;
+constexpr int VL_E1_DEFAULT = 11, VL_E2_DEFAULT = 13;  // M1 <= 1016, M2 <= 4088
+
+__host__ __device__ __forceinline__ int64_t vl_class_max(int edge) {
+    return (int64_t(1) << (edge - 1)) - VL_M;
+}
 
 struct VarlenWork {
     unsigned long long next_long;   // work counters: class L
@@ -66,12 +74,12 @@ inline size_t varlen_ws_bytes(int64_t nsys) {
 // ceil(log2 n) (0 for n <= 1), raised so that each class occupies whole
 // buckets: S <= 8, M1 9..10, M2 11..12, L >= 13 (every length fits its class:
 // 2^8 = 256 > 248, 2^10 = 1024 > 1016, 2^12 = 4096 > 4088).
-__device__ __forceinline__ int len_bucket(int64_t n) {
+__device__ __forceinline__ int len_bucket(int64_t n, int e1, int e2) {
     if (n <= 1) return 0;
     int b = 64 - __clzll((unsigned long long)(n - 1));
     if (n > VL_SHORT_N && b < VL_B_M1) b = VL_B_M1;
-    if (n > VL_M1_N && b < VL_B_M2) b = VL_B_M2;
-    if (n > VL_M2_N && b < VL_B_L) b = VL_B_L;
+    if (e1 > VL_B_M1 && n > vl_class_max(e1) && b < e1) b = e1;
+    if (n > vl_class_max(e2) && b < e2) b = e2;
     return b < VL_BUCKETS ? b : VL_BUCKETS - 1;
 }
 
@@ -110,21 +118,21 @@ __device__ __forceinline__ int64_t plan_len(const int64_t *__restrict__ offsets,
 
 __global__ void __launch_bounds__(VL_PLAN_THREADS)
 k_varlen_hist(const int64_t *__restrict__ offsets, int64_t nsys, int64_t total, VarlenWork *work,
-              int *status) {
+              int *status, int e1, int e2) {
     __shared__ unsigned long long hist[VL_BUCKETS];
     const int tid = threadIdx.x;
     if (tid < VL_BUCKETS) hist[tid] = 0;
     __syncthreads();
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + tid; k < nsys;
          k += int64_t(gridDim.x) * blockDim.x)
-        atomicAdd(&hist[len_bucket(plan_len(offsets, k, total, status, true))], 1ull);
+        atomicAdd(&hist[len_bucket(plan_len(offsets, k, total, status, true), e1, e2)], 1ull);
     __syncthreads();
     if (tid < VL_BUCKETS && hist[tid]) atomicAdd(&work->hist[tid], hist[tid]);
 }
 
 __global__ void __launch_bounds__(VL_PLAN_THREADS)
 k_varlen_scatter(const int64_t *__restrict__ offsets, int64_t nsys, int64_t total,
-                 VarlenWork *work, longlong2 *__restrict__ meta) {
+                 VarlenWork *work, longlong2 *__restrict__ meta, int e1, int e2) {
     __shared__ unsigned long long hist[VL_BUCKETS];
     __shared__ unsigned long long start[VL_BUCKETS];
     const int tid = threadIdx.x;
@@ -136,7 +144,7 @@ k_varlen_scatter(const int64_t *__restrict__ offsets, int64_t nsys, int64_t tota
         int b = -1;
         unsigned long long local = 0;
         if (k < nsys) {
-            b = len_bucket(plan_len(offsets, k, total, nullptr, false));
+            b = len_bucket(plan_len(offsets, k, total, nullptr, false), e1, e2);
             local = atomicAdd(&hist[b], 1ull);
         }
         __syncthreads();
@@ -342,7 +350,9 @@ template <typename T>
 __global__ void __launch_bounds__(VL_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c, const T *d,
                T *out, int accumulate, int64_t nsys, int64_t total, int64_t max_len,
-               VarlenWork *work, const longlong2 *__restrict__ meta, int nlevels, int *status) {
+               VarlenWork *work, const longlong2 *__restrict__ meta, int nlevels, int *status,
+               int e1, int e2) {
+    const int64_t m1_max = vl_class_max(e1), m2_max = vl_class_max(e2);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ VItem s_it[2];
     __shared__ VItem s_team_it[VL_THREADS / VL_TEAM][2];
@@ -361,9 +371,9 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int helper = blockDim.x - 1;
-    const int64_t n_l = int64_t(n_in_buckets(work, VL_B_L, VL_BUCKETS));
-    const int64_t n_m2 = int64_t(n_in_buckets(work, VL_B_M2, VL_B_L));
-    const int64_t n_m1 = int64_t(n_in_buckets(work, VL_B_M1, VL_B_M2));
+    const int64_t n_l = int64_t(n_in_buckets(work, e2, VL_BUCKETS));
+    const int64_t n_m2 = int64_t(n_in_buckets(work, e1, e2));
+    const int64_t n_m1 = int64_t(n_in_buckets(work, VL_B_M1, e1));
     const int64_t n_s = nsys - n_l - n_m2 - n_m1;
 
     // ---- class L: one system per block, two passes
@@ -415,7 +425,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         unsigned long long nx_item = 0;
         if (tid == helper) nx_item = atomicAdd(&work->next_m2, 1ull);
         const int64_t s0 = it.s0, n = it.n;
-        const bool ok = sys_valid(s0, n, total) && n <= VL_M2_N;
+        const bool ok = sys_valid(s0, n, total) && n <= m2_max;
         if (!ok && tid == 0 && status) atomicCAS(status, 0, int(TRID_ERR_INVALID_ARG));
         const int pad = sys_pad<T>(s0);
         const int ntiles = ok ? int((n + pad + VL_M - 1) / VL_M) : 0;  // <= blockDim.x
@@ -459,7 +469,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             unsigned long long nx_item = 0;
             if (tt == thelper) nx_item = atomicAdd(&work->next_m1, 1ull);
             const int64_t s0 = it.s0, n = it.n;
-            const bool ok = sys_valid(s0, n, total) && n <= VL_M1_N;
+            const bool ok = sys_valid(s0, n, total) && n <= m1_max;
             if (!ok && tt == 0 && status) atomicCAS(status, 0, int(TRID_ERR_INVALID_ARG));
             const int pad = sys_pad<T>(s0);
             const int ntiles = ok ? int((n + pad + VL_M - 1) / VL_M) : 0;  // <= VL_TEAM
@@ -547,7 +557,7 @@ static bool varlen_levels(int64_t max_len, int &nlevels, size_t &smem) {
 template <typename T>
 static trid_status varlen_run(const T *a, const T *b, const T *c, const T *d, T *out, int acc,
                               const int64_t *offsets, int64_t nsys, int64_t total, int64_t max_len,
-                              void *ws, cudaStream_t st) {
+                              void *ws, cudaStream_t st, int e1, int e2) {
     int nlevels = 0;
     size_t smem = 0;
     if (!varlen_levels<T>(max_len, nlevels, smem)) return TRID_ERR_UNSUPPORTED;
@@ -561,9 +571,9 @@ static trid_status varlen_run(const T *a, const T *b, const T *c, const T *d, T 
     if (pblocks > 4 * int64_t(di->sm_count)) pblocks = 4 * int64_t(di->sm_count);
     if (cudaMemsetAsync(work, 0, sizeof(VarlenWork), st) != cudaSuccess) return TRID_ERR_CUDA;
     k_varlen_hist<<<dim3(unsigned(pblocks)), VL_PLAN_THREADS, 0, st>>>(offsets, nsys, total, work,
-                                                                      device_status_word());
+                                                                      device_status_word(), e1, e2);
     k_varlen_scatter<<<dim3(unsigned(pblocks)), VL_PLAN_THREADS, 0, st>>>(offsets, nsys, total,
-                                                                         work, meta);
+                                                                         work, meta, e1, e2);
     if (cudaGetLastError() != cudaSuccess) return TRID_ERR_CUDA;
     auto kern = k_varlen_solve<T>;
     const int per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), VL_THREADS, smem);
@@ -571,7 +581,7 @@ static trid_status varlen_run(const T *a, const T *b, const T *c, const T *d, T 
     int64_t grid = int64_t(di->sm_count) * per_sm;
     kern<<<dim3(unsigned(grid)), VL_THREADS, smem, st>>>(a, b, c, d, out, acc, nsys, total,
                                                          max_len, work, meta, nlevels,
-                                                         device_status_word());
+                                                         device_status_word(), e1, e2);
     return cudaGetLastError() == cudaSuccess ? TRID_OK : TRID_ERR_CUDA;
 }
 
@@ -584,13 +594,30 @@ extern "C" size_t trid_solve_varlen_workspace_bytes(int64_t nsys) {
     return varlen_ws_bytes(nsys);
 }
 
-extern "C" trid_status trid_solve_batch_varlen(const void *a, const void *b, const void *c,
-                                               void *d, void *u, const int64_t *offsets,
-                                               int64_t nsys, int64_t total, int64_t max_len,
-                                               trid_dtype dtype, void *workspace,
-                                               size_t workspace_bytes, trid_stream_t stream) {
+// Class edges of a configuration (see trid_varlen_config in include/trid.h).
+static bool vl_edges(const trid_varlen_config *cfg, int &e1, int &e2) {
+    if (!cfg) { e1 = VL_E1_DEFAULT; e2 = VL_E2_DEFAULT; return true; }
+    auto edge_of = [](int32_t len, int &e) {
+        for (int k = VL_B_M1; k <= VL_E2_DEFAULT; ++k)
+            if (vl_class_max(k) == len) { e = k; return true; }
+        return false;
+    };
+    if (cfg->team_max == VL_SHORT_N) e1 = VL_B_M1;
+    else if (!edge_of(cfg->team_max, e1) || e1 > VL_E1_DEFAULT) return false;
+    if (cfg->block_max == cfg->team_max) e2 = e1;
+    else if (!edge_of(cfg->block_max, e2) || e2 > VL_E2_DEFAULT || e2 < e1) return false;
+    return true;
+}
+
+static trid_status varlen_entry(const void *a, const void *b, const void *c, void *d, void *u,
+                                const int64_t *offsets, int64_t nsys, int64_t total,
+                                int64_t max_len, trid_dtype dtype, void *workspace,
+                                size_t workspace_bytes, trid_stream_t stream,
+                                const trid_varlen_config *cfg) {
     if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
     if (nsys < 0 || total < 0 || max_len < 0) return TRID_ERR_INVALID_ARG;
+    int e1, e2;
+    if (!vl_edges(cfg, e1, e2)) return TRID_ERR_INVALID_ARG;
     if (nsys == 0 || total == 0) return TRID_OK;
     if (!a || !b || !c || !d || !offsets) return TRID_ERR_INVALID_ARG;
     const size_t esz = dtype == TRID_F32 ? 4 : 8;
@@ -615,9 +642,102 @@ extern "C" trid_status trid_solve_batch_varlen(const void *a, const void *b, con
         return varlen_run<float>(static_cast<const float *>(a), static_cast<const float *>(b),
                                  static_cast<const float *>(c), static_cast<const float *>(d),
                                  static_cast<float *>(u ? u : d), acc, offsets, nsys, total,
-                                 max_len, workspace, st);
+                                 max_len, workspace, st, e1, e2);
     return varlen_run<double>(static_cast<const double *>(a), static_cast<const double *>(b),
                               static_cast<const double *>(c), static_cast<const double *>(d),
                               static_cast<double *>(u ? u : d), acc, offsets, nsys, total,
-                              max_len, workspace, st);
+                              max_len, workspace, st, e1, e2);
+}
+
+extern "C" trid_status trid_solve_batch_varlen(const void *a, const void *b, const void *c,
+                                               void *d, void *u, const int64_t *offsets,
+                                               int64_t nsys, int64_t total, int64_t max_len,
+                                               trid_dtype dtype, void *workspace,
+                                               size_t workspace_bytes, trid_stream_t stream) {
+    return varlen_entry(a, b, c, d, u, offsets, nsys, total, max_len, dtype, workspace,
+                        workspace_bytes, stream, nullptr);
+}
+
+extern "C" trid_status trid_solve_batch_varlen_cfg(const void *a, const void *b, const void *c,
+                                                   void *d, void *u, const int64_t *offsets,
+                                                   int64_t nsys, int64_t total, int64_t max_len,
+                                                   trid_dtype dtype, void *workspace,
+                                                   size_t workspace_bytes, trid_stream_t stream,
+                                                   const trid_varlen_config *cfg) {
+    return varlen_entry(a, b, c, d, u, offsets, nsys, total, max_len, dtype, workspace,
+                        workspace_bytes, stream, cfg);
+}
+
+extern "C" size_t trid_varlen_autotune_workspace_bytes(int64_t nsys, int64_t total,
+                                                       trid_dtype dtype) {
+    if (nsys < 0 || total < 0 || (dtype != TRID_F32 && dtype != TRID_F64)) return 0;
+    const size_t esz = dtype == TRID_F32 ? 4 : 8;
+    return (varlen_ws_bytes(nsys) + 255) / 256 * 256 + size_t(total) * esz;
+}
+
+// Time every admissible configuration on the caller's batch (on a scratch
+// copy of d, so d is not modified) and return the fastest.
+extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const void *c,
+                                            const void *d, const int64_t *offsets, int64_t nsys,
+                                            int64_t total, int64_t max_len, trid_dtype dtype,
+                                            void *workspace, size_t workspace_bytes,
+                                            trid_stream_t stream, trid_varlen_config *best,
+                                            float *best_ms) {
+    if (!best) return TRID_ERR_INVALID_ARG;
+    best->team_max = int32_t(vl_class_max(VL_E1_DEFAULT));
+    best->block_max = int32_t(vl_class_max(VL_E2_DEFAULT));
+    if (best_ms) *best_ms = 0.0f;
+    if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
+    if (nsys < 0 || total < 0 || max_len < 0) return TRID_ERR_INVALID_ARG;
+    if (nsys == 0 || total == 0) return TRID_OK;
+    if (!a || !b || !c || !d || !offsets) return TRID_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < trid_varlen_autotune_workspace_bytes(nsys, total, dtype))
+        return TRID_ERR_ALLOC;
+    if ((reinterpret_cast<uintptr_t>(workspace) % 256) != 0) return TRID_ERR_MISALIGNED;
+    const size_t esz = dtype == TRID_F32 ? 4 : 8;
+    const size_t wsb = (varlen_ws_bytes(nsys) + 255) / 256 * 256;
+    void *scratch = static_cast<char *>(workspace) + wsb;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t teams[3] = {VL_SHORT_N, int32_t(vl_class_max(10)), int32_t(vl_class_max(11))};
+    const int32_t blocks[4] = {int32_t(vl_class_max(11)), int32_t(vl_class_max(12)),
+                               int32_t(vl_class_max(13)), 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return TRID_ERR_CUDA;
+    }
+    float best_t = -1.0f;
+    trid_status rs = TRID_OK;
+    for (int ti = 0; ti < 3 && rs == TRID_OK; ++ti) {
+        for (int bi = 0; bi < 4 && rs == TRID_OK; ++bi) {
+            if (bi < 3 && blocks[bi] == teams[ti]) continue;  // same as bi == 3
+            trid_varlen_config cfg{teams[ti], bi == 3 ? teams[ti] : blocks[bi]};
+            int ea, eb;
+            if (!vl_edges(&cfg, ea, eb)) continue;
+            float t_best = -1.0f;
+            for (int rep = 0; rep < 4 && rs == TRID_OK; ++rep) {  // first run warms up
+                if (cudaMemcpyAsync(scratch, d, size_t(total) * esz, cudaMemcpyDeviceToDevice,
+                                    st) != cudaSuccess) { rs = TRID_ERR_CUDA; break; }
+                cudaEventRecord(e0, st);
+                rs = varlen_entry(a, b, c, scratch, nullptr, offsets, nsys, total, max_len, dtype,
+                                  workspace, wsb, stream, &cfg);
+                cudaEventRecord(e1, st);
+                if (rs != TRID_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rs = TRID_ERR_CUDA; break; }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && (t_best < 0.0f || ms < t_best)) t_best = ms;
+            }
+            if (rs == TRID_OK && t_best >= 0.0f && (best_t < 0.0f || t_best < best_t)) {
+                best_t = t_best;
+                *best = cfg;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != TRID_OK) { launch_ok(); return rs; }
+    if (best_ms) *best_ms = best_t;
+    return launch_ok() ? TRID_OK : TRID_ERR_CUDA;
 }

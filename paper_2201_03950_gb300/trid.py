@@ -61,6 +61,9 @@ def _bind(L):
         "trid_solve_workspace_bytes": ([P, i32, i32, i32], sz),
         "trid_solve_batch_varlen": ([P, P, P, P, P, P, i64, i64, i64, i32, P, sz, P], i32),
         "trid_solve_varlen_workspace_bytes": ([i64], sz),
+        "trid_solve_batch_varlen_cfg": ([P, P, P, P, P, P, i64, i64, i64, i32, P, sz, P, P], i32),
+        "trid_varlen_autotune_workspace_bytes": ([i64, i64, i32], sz),
+        "trid_varlen_autotune": ([P, P, P, P, P, i64, i64, i64, i32, P, sz, P, P, P], i32),
         "trid_solve_batch_adjoint": ([P, P, P, P, P, P, P, P, P, P, i32, i32, i32, P, sz, P], i32),
         "trid_adjoint_workspace_bytes": ([P, i32, i32, i32], sz),
         "adi_step": ([P, P, i32, f64, i32, i32, P, sz, P], i32),
@@ -186,25 +189,66 @@ def varlen_workspace_bytes(nsys: int) -> int:
     return int(load().trid_solve_varlen_workspace_bytes(int(nsys)))
 
 
-def solve_varlen(a, b, c, d, offsets, max_len: int, u=None, workspace=None, stream=None):
+class VarlenConfig(ctypes.Structure):
+    """Length classes of the uneven-batch solver (trid_varlen_config)."""
+    _fields_ = [("team_max", ctypes.c_int32), ("block_max", ctypes.c_int32)]
+
+    def __repr__(self):
+        return f"VarlenConfig(team_max={self.team_max}, block_max={self.block_max})"
+
+
+def _check_offsets(offsets):
+    import torch
+    if not (offsets.is_cuda and offsets.dtype == torch.int64 and offsets.is_contiguous()):
+        raise ValueError("offsets must be a contiguous int64 CUDA tensor")
+
+
+def solve_varlen(a, b, c, d, offsets, max_len: int, u=None, workspace=None, stream=None,
+                 config: VarlenConfig | None = None):
     """Batch of systems of different lengths: system k occupies rows
-    [offsets[k], offsets[k+1]) (offsets: int64 CUDA tensor of nsys + 1)."""
+    [offsets[k], offsets[k+1]) (offsets: int64 CUDA tensor of nsys + 1).
+    ``config``: length classes (e.g. from ``varlen_autotune``); None = defaults."""
     import torch
     total = d.numel()
     _check_tensors((a, b, c, d, u), d, total)
-    if not (offsets.is_cuda and offsets.dtype == torch.int64 and offsets.is_contiguous()):
-        raise ValueError("offsets must be a contiguous int64 CUDA tensor")
+    _check_offsets(offsets)
     nsys = offsets.numel() - 1
     L = load()
     if workspace is None:
         workspace = torch.empty(varlen_workspace_bytes(max(nsys, 0)), dtype=torch.uint8,
                                 device=d.device)
-    st = L.trid_solve_batch_varlen(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(u), _ptr(offsets),
-                                   int(nsys), int(total), int(max_len), _dtype(d), _ptr(workspace),
-                                   workspace.numel() * workspace.element_size(), _stream(stream))
+    args = (_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(u), _ptr(offsets), int(nsys), int(total),
+            int(max_len), _dtype(d), _ptr(workspace), workspace.numel() * workspace.element_size(),
+            _stream(stream))
+    if config is None:
+        st = L.trid_solve_batch_varlen(*args)
+    else:
+        st = L.trid_solve_batch_varlen_cfg(*args, ctypes.byref(config))
     if st != 0:
         raise TridError(st, "trid_solve_batch_varlen")
     return u if u is not None else d
+
+
+def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None):
+    """Time every admissible length-class configuration on this batch (d is
+    not modified) and return (best VarlenConfig, its time in ms)."""
+    import torch
+    total = d.numel()
+    _check_tensors((a, b, c, d), d, total)
+    _check_offsets(offsets)
+    nsys = offsets.numel() - 1
+    L = load()
+    ws = torch.empty(max(int(L.trid_varlen_autotune_workspace_bytes(nsys, total, _dtype(d))), 1),
+                     dtype=torch.uint8, device=d.device)
+    best = VarlenConfig()
+    ms = ctypes.c_float(0.0)
+    st = L.trid_varlen_autotune(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(offsets), int(nsys),
+                                int(total), int(max_len), _dtype(d), _ptr(ws),
+                                ws.numel(), _stream(stream), ctypes.byref(best),
+                                ctypes.byref(ms))
+    if st != 0:
+        raise TridError(st, "trid_varlen_autotune")
+    return best, float(ms.value)
 
 
 def solve_workspace_bytes(dims, solve_dim: int, dtype) -> int:

@@ -136,3 +136,56 @@ def test_varlen_full_size_config_sampled():
     r[:-1] += torch.where(last[:-1], 0.0, C[:-1] * X[1:])
     res = ((r - D).abs().max() / ((A.abs() + B.abs() + C.abs()).max() * X.abs().max() + D.abs().max())).item()
     assert res <= 1e-5
+
+
+CLASS_EDGES = [248, 249, 503, 504, 505, 1015, 1016, 1017, 2039, 2040, 2041, 4087, 4088, 4089,
+               5000, 1, 2, 200]
+CONFIGS = [(248, 248), (248, 1016), (248, 2040), (248, 4088), (504, 504), (504, 1016),
+           (504, 2040), (504, 4088), (1016, 1016), (1016, 2040), (1016, 4088)]
+
+
+def run_cfg(lengths, dtype, cfg, seed=3):
+    lengths = np.asarray(lengths, dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    total = int(off[-1])
+    a, b, c, d = inputs.dominant_system((total,), seed=seed, dtype=dtype)
+    ref = oracle.solve_varlen(a, b, c, d, off)
+    ta, tb, tc, td = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (a, b, c, d))
+    toff = torch.from_numpy(off).cuda()
+    trid.solve_varlen(ta, tb, tc, td, toff, int(lengths.max()),
+                      config=trid.VarlenConfig(*cfg))
+    torch.cuda.synchronize()
+    return td.cpu().numpy(), ref, off
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=[f"team{a}-block{b}" for a, b in CONFIGS])
+def test_varlen_every_class_configuration(cfg):
+    """Every admissible class split routes each length (incl. the class
+    boundaries, each side) to a path that solves it exactly."""
+    got, ref, off = run_cfg(CLASS_EDGES, np.float32, cfg)
+    assert per_system_err(got, ref, off) <= TOL[np.float32]
+
+
+def test_varlen_autotune_picks_a_valid_config_and_keeps_d():
+    lengths = inputs.loguniform_lengths(600, 16, 16384, seed=9)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    total = int(off[-1])
+    a, b, c, d = inputs.dominant_system((total,), seed=5, dtype=np.float32)
+    ta, tb, tc, td = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (a, b, c, d))
+    toff = torch.from_numpy(off).cuda()
+    cfg, ms = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()))
+    assert (cfg.team_max, cfg.block_max) in CONFIGS
+    assert ms > 0.0
+    assert np.array_equal(td.cpu().numpy(), d)  # the autotuner works on a copy
+    trid.solve_varlen(ta, tb, tc, td, toff, int(lengths.max()), config=cfg)
+    torch.cuda.synchronize()
+    ref = oracle.solve_varlen(a, b, c, d, off)
+    assert per_system_err(td.cpu().numpy(), ref, off) <= TOL[np.float32]
+
+
+def test_varlen_invalid_config_rejected():
+    t = torch.zeros(8, device="cuda")
+    toff = torch.tensor([0, 8], dtype=torch.int64, device="cuda")
+    for bad in ((300, 4088), (1016, 504), (2040, 4088), (504, 9000)):
+        with pytest.raises(trid.TridError):
+            trid.solve_varlen(t, t + 2, t, t, toff, 8, config=trid.VarlenConfig(*bad))
