@@ -291,16 +291,18 @@ k_adi_z_ysub(const __grid_constant__ TmaSet maps,
         const T *se = reinterpret_cast<const T *>(smem + s * stage_bytes);
         const T *sxs = reinterpret_cast<const T *>(smem + s * stage_bytes + slot_bytes);
         const T *sxe = reinterpret_cast<const T *>(smem + s * stage_bytes + 2 * slot_bytes);
-        const int mesh = int(bt / nbox);
-        const int f0 = int(bt - int64_t(mesh) * nbox) * SG;
+        const int b32 = int(bt), nb32 = int(nbox);
+        const int mesh = b32 / nb32;
+        const int f0 = (b32 - mesh * nb32) * SG;
         const int r = (f0 / nx) % M;
         const T al = ys.alpha[r], be = ys.beta[r];
+        // n is a multiple of M: a tile is entirely inside the line or padding
+        const bool tin = ok && i0 < n;
         T d[M];
 #pragma unroll
         for (int j = 0; j < M; ++j) {
-            const int i = i0 + j;
-            const int o = i * SG + sl;
-            d[j] = (ok && i < n) ? fma(be, sxe[o], fma(al, sxs[o], se[o])) : T(0);
+            const int o = (i0 + j) * SG + sl;
+            d[j] = tin ? fma(be, sxe[o], fma(al, sxs[o], se[o])) : T(0);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -324,11 +326,10 @@ k_adi_z_ysub(const __grid_constant__ TmaSet maps,
         static_tile_substitute<T, M>(st, d, s_xs[w], s_xe[w]);
         if (first) d[0] = b0;
         if (last) d[M - 1] = b1;
-        if (ok) {
-            T *ob = out + (size_t(mesh) * n * nplane + f0 + sl);
+        if (tin) {
+            T *ob = out + (size_t(mesh) * n + i0) * nplane + f0 + sl;
 #pragma unroll
-            for (int j = 0; j < M; ++j)
-                if (i0 + j < n) ob[size_t(i0 + j) * nplane] = d[j];
+            for (int j = 0; j < M; ++j, ob += nplane) *ob = d[j];
         }
     }
 }
