@@ -117,7 +117,7 @@ k_adi_xy(const T *__restrict__ u, T *__restrict__ e, T *__restrict__ rs, T *__re
             }
             T ds, de, xs, xe;
             static_tile_reduce<T, M>(sx, d, firstx, lastx, ds, de);
-            static_group_solve_tab<T, G>(lane_tab, ds, de, g, xs, xe);
+            static_group_solve_tab<T, G>(lane_tab, ds, de, g, xs, xe, sx.rounds);
             static_tile_substitute<T, M>(sx, d, xs, xe);
             if (act) {
                 store_contig_vec<T, M>(sd + r * nx + x0, d);
@@ -318,7 +318,7 @@ k_adi_z_ysub(const __grid_constant__ TmaSet maps,
         named_barrier(1, NCONS);
         {
             T xs, xe;
-            static_group_solve<T, NT>(LS, s_ds[q], s_de[q], rt, xs, xe);
+            static_group_solve<T, NT>(LS, s_ds[q], s_de[q], rt, xs, xe, st.rounds);
             s_xs[q] = xs;
             s_xe[q] = xe;
         }

@@ -38,6 +38,7 @@ struct AdiStatics {
     T XAS[32], XCS[32];
     int ntiles;      // G = tiles per line (power of two <= 32)
     int real_tiles;  // n / 8; tiles beyond are zero padding
+    int rounds;      // PCR rounds executed (see adi_static_fill)
 };
 
 // Host: fill the tables for a line of n nodes (n % M == 0, M <= n <= 32 M).
@@ -106,9 +107,17 @@ inline bool adi_static_fill(AdiStatics<T, AS_M> &s, int n, double lam, double *r
         s.XAS[g] = T(as_g[g]);
         s.XCS[g] = T(cs_g[g]);
     }
+    // A PCR round whose coupling coefficients are all below 2^-(p+4) (p the
+    // significand bits of T) changes no result by more than 1/16 ulp; for a
+    // diagonally dominant constant operator the coupling falls geometrically
+    // from round to round (each round squares it), so the rounds from the
+    // first such one on are not executed.
+    const double negligible = sizeof(T) == 4 ? 1.0 / double(1 << 28) : 1.0 / 144115188075855872.0;
+    s.rounds = AS_ROUNDS;
     for (int k = 0; k < AS_ROUNDS; ++k) {
         const int st = 1 << k;
         double na[32], nc[32];
+        double coup = 0.0;
         for (int g = 0; g < 32; ++g) {
             if (st >= Gt) {  // unused round: identity
                 s.PR[k][g] = T(1); s.PA[k][g] = T(0); s.PC[k][g] = T(0);
@@ -121,10 +130,13 @@ inline bool adi_static_fill(AdiStatics<T, AS_M> &s, int n, double lam, double *r
             s.PR[k][g] = T(r);
             s.PA[k][g] = T(r * ra[g]);
             s.PC[k][g] = T(r * rc[g]);
+            coup = fmax(coup, fmax(fabs(r * ra[g]), fabs(r * rc[g])));
+            coup = fmax(coup, fabs(r - 1.0));
             na[g] = -r * (ra[g] * am);
             nc[g] = -r * (rc[g] * cp);
         }
         for (int g = 0; g < 32; ++g) { ra[g] = na[g]; rc[g] = nc[g]; }
+        if (s.rounds == AS_ROUNDS && st < Gt && coup < negligible) s.rounds = k;
     }
     return true;
 }
@@ -198,7 +210,7 @@ __device__ __forceinline__ void static_tile_substitute(const AdiStatics<T, AS_M>
 // of the warp must call it.
 template <typename T, int G>
 __device__ __forceinline__ void static_group_solve(const LaneStatics<T> &L, T ds, T de, int g,
-                                                   T &xs, T &xe) {
+                                                   T &xs, T &xe, int rounds = AS_ROUNDS) {
     constexpr unsigned FULL = 0xffffffffu;
     T nds = __shfl_down_sync(FULL, ds, 1, G);
     if (g + 1 >= G) nds = T(0);
@@ -206,7 +218,7 @@ __device__ __forceinline__ void static_group_solve(const LaneStatics<T> &L, T ds
 #pragma unroll
     for (int k = 0; k < AS_ROUNDS; ++k) {
         const int st = 1 << k;
-        if (st >= G) break;
+        if (st >= G || k >= rounds) break;
         T dm = __shfl_up_sync(FULL, rd, st, G);
         T dp = __shfl_down_sync(FULL, rd, st, G);
         if (g < st) dm = T(0);
@@ -223,7 +235,7 @@ __device__ __forceinline__ void static_group_solve(const LaneStatics<T> &L, T ds
 // (lane g reads column g: conflict-free) instead of holding them in registers.
 template <typename T, int G>
 __device__ __forceinline__ void static_group_solve_tab(const T (*tab)[32], T ds, T de, int g,
-                                                       T &xs, T &xe) {
+                                                       T &xs, T &xe, int rounds = AS_ROUNDS) {
     constexpr unsigned FULL = 0xffffffffu;
     T nds = __shfl_down_sync(FULL, ds, 1, G);
     if (g + 1 >= G) nds = T(0);
@@ -231,7 +243,7 @@ __device__ __forceinline__ void static_group_solve_tab(const T (*tab)[32], T ds,
 #pragma unroll
     for (int k = 0; k < AS_ROUNDS; ++k) {
         const int st = 1 << k;
-        if (st >= G) break;
+        if (st >= G || k >= rounds) break;
         T dm = __shfl_up_sync(FULL, rd, st, G);
         T dp = __shfl_down_sync(FULL, rd, st, G);
         if (g < st) dm = T(0);
@@ -338,7 +350,7 @@ k_adi_x_static(const T *__restrict__ u, T *__restrict__ w, int nx, int ny, int n
         }
         T ds, de, xs, xe;
         static_tile_reduce<T, M>(st, d, first, last, ds, de);
-        static_group_solve<T, G>(L, ds, de, g, xs, xe);
+        static_group_solve<T, G>(L, ds, de, g, xs, xe, st.rounds);
         static_tile_substitute<T, M>(st, d, xs, xe);
         if (act) {
             if (x0 + M <= nx) {
@@ -461,7 +473,7 @@ k_adi_strided_static(const __grid_constant__ TmaSet maps,
         named_barrier(1, NCONS);
         {
             T xs, xe;
-            static_group_solve<T, NT>(LS, s_ds[q], s_de[q], rt, xs, xe);
+            static_group_solve<T, NT>(LS, s_ds[q], s_de[q], rt, xs, xe, st.rounds);
             s_xs[q] = xs;
             s_xe[q] = xe;
         }
