@@ -108,9 +108,19 @@ __device__ __forceinline__ void group_solve(T as, T cs, T ds, T ae, T ce, T de, 
         const T r = rcp(rdiag);
         ra *= r; rc *= r; rd *= r;
     }
-    // parallel cyclic reduction over the G unit-diagonal rows
+    // parallel cyclic reduction over the G unit-diagonal rows.  Each round
+    // squares the coupling of a diagonally dominant reduced system; once every
+    // |ra|, |rc| of the warp is below 2^-(p+4) (p the significand bits), the
+    // remaining rounds change no value by more than 1/16 ulp (normwise), and
+    // the warp stops.
+    constexpr float negligible = sizeof(T) == 4 ? 3.7252903e-09f : 6.9388939e-18f;
 #pragma unroll
     for (int s = 1; s < G; s <<= 1) {
+        if (G >= 8) {
+            const float cpl = float(fmax(fabs(ra), fabs(rc)));
+            const unsigned top = __reduce_max_sync(FULL, __float_as_uint(cpl));
+            if (__uint_as_float(top) < negligible) break;
+        }
         T am = __shfl_up_sync(FULL, ra, s, G);
         T cm = __shfl_up_sync(FULL, rc, s, G);
         T dm = __shfl_up_sync(FULL, rd, s, G);
