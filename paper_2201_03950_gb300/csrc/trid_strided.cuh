@@ -218,8 +218,9 @@ k_strided_tma(const __grid_constant__ TmaSet maps, Coef coef, T *out, Lines L, i
                     break;
                 }
                 mbar_expect_tx(&full[s], tx);
-                const int x0 = int((bt % nxc) * SG);
-                const int o = int(bt / nxc);
+                const int b32 = int(bt), n32 = int(nxc);  // nbatch < 2^31 (host)
+                const int o = b32 / n32;
+                const int x0 = (b32 - o * n32) * SG;
                 unsigned char *dst = smem + s * stage_bytes;
 #pragma unroll
                 for (int q = 0; q < NSLOT; ++q)
@@ -236,6 +237,8 @@ k_strided_tma(const __grid_constant__ TmaSet maps, Coef coef, T *out, Lines L, i
     const bool full_tile = (i0 + M <= n);
     const int w = tile * P + sl;
     const int stride = int(L.stride);
+    const int inner32 = int(L.inner);
+    const size_t inner_n = size_t(L.inner) * size_t(L.n);
     int k = 0;
     for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x, ++k) {
         const int s = k % stages;
@@ -250,9 +253,10 @@ k_strided_tma(const __grid_constant__ TmaSet maps, Coef coef, T *out, Lines L, i
         const T *sc = reinterpret_cast<const T *>(stg + 2 * slot_bytes);
         const T *sd = reinterpret_cast<const T *>(stg + Coef::NCOEF * slot_bytes);
         const T *su = reinterpret_cast<const T *>(stg + (Coef::NCOEF + 1) * slot_bytes);
-        const int64_t x = (bt % nxc) * SG + sl;
-        const int64_t o = bt / nxc;
-        const bool active = ok && x < L.inner;
+        const int b32 = int(bt), n32 = int(nxc);  // nbatch < 2^31 (host)
+        const int o = b32 / n32;
+        const int x = (b32 - o * n32) * SG + sl;
+        const bool active = ok && x < inner32;
         T ra[M], rb[M], rc[M], rd[M], ru[M];
 #pragma unroll
         for (int j = 0; j < M; ++j) {
@@ -286,7 +290,7 @@ k_strided_tma(const __grid_constant__ TmaSet maps, Coef coef, T *out, Lines L, i
         named_barrier(1, NCONS);
         tile_substitute<T, M>(ra, rc, rd, s_xs[w], s_xe[w]);
         if (active) {
-            T *ob = out + (x + o * L.inner * L.n);
+            T *ob = out + (size_t(o) * inner_n + x);
 #pragma unroll
             for (int j = 0; j < M; ++j)
                 if (full_tile || i0 + j < n) ob[(i0 + j) * stride] = ACC ? rd[j] + ru[j] : rd[j];
@@ -348,6 +352,8 @@ inline bool launch_strided_tma(const void *const *arrs, Coef coef, T *out, const
     const int per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), NT * SG + 32, smem);
     if (per_sm < 1) return false;
     const int64_t nbatch = (L.inner + SG - 1) / SG * outer;
+    // the kernel indexes batches and lines with 32-bit integers
+    if (nbatch >= (int64_t(1) << 31) || L.inner >= (int64_t(1) << 31)) return false;
     const int64_t slots = int64_t(di->sm_count) * per_sm;
     const int64_t grid = nbatch < slots ? nbatch : slots;
     kern<<<dim3(unsigned(grid)), NT * SG + 32, smem, st>>>(maps, coef, out, L, nbatch, stages,
