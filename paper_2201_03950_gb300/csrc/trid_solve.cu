@@ -145,6 +145,8 @@ __device__ __forceinline__ void long_load(const T *__restrict__ a, const T *__re
     }
 }
 
+// Thread -> (system, tile).  With every index below 2^31 (checked on the
+// host: nsys * ntiles and the line geometry) the divisions run in 32 bits.
 template <bool STRIDED>
 __device__ __forceinline__ void long_index(const Lines &L, int64_t ntiles, int64_t &sys,
                                            int64_t &tile) {
@@ -152,10 +154,20 @@ __device__ __forceinline__ void long_index(const Lines &L, int64_t ntiles, int64
         sys = int64_t(blockIdx.x) * 32 + (threadIdx.x & 31);
         tile = int64_t(blockIdx.y) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     } else {
-        const int64_t gidx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-        sys = gidx / ntiles;
-        tile = gidx % ntiles;
+        const int g32 = int(blockIdx.x * blockDim.x + threadIdx.x);
+        const int nt = int(ntiles);
+        const int q = g32 / nt;
+        sys = q;
+        tile = g32 - q * nt;
     }
+}
+
+// First element of line `sys` (32-bit division, as above).
+__device__ __forceinline__ int64_t line_base32(const Lines &L, int64_t sys) {
+    if (L.inner == 1) return sys * L.n;
+    const int s32 = int(sys), in32 = int(L.inner);
+    const int q = s32 / in32;
+    return int64_t(s32 - q * in32) + int64_t(q) * L.inner * L.n;
 }
 
 template <typename T, int M, bool STRIDED>
@@ -166,7 +178,7 @@ k_long_reduce(const T *__restrict__ a, const T *__restrict__ b, const T *__restr
     int64_t sys, tile;
     long_index<STRIDED>(L, ntiles, sys, tile);
     if (sys >= L.nsys || tile >= ntiles) return;
-    const int64_t base = L.base(sys);
+    const int64_t base = line_base32(L, sys);
     const int64_t i0 = tile * M;
     T ra[M], rb[M], rc[M], rd[M];
     long_load<T, M>(a, b, c, d, L, base, i0, vec_ok, ra, rb, rc, rd);
@@ -188,7 +200,7 @@ k_long_subst(const T *__restrict__ a, const T *__restrict__ b, const T *__restri
     int64_t sys, tile;
     long_index<STRIDED>(L, ntiles, sys, tile);
     if (sys >= L.nsys || tile >= ntiles) return;
-    const int64_t base = L.base(sys);
+    const int64_t base = line_base32(L, sys);
     const int64_t i0 = tile * M;
     T ra[M], rb[M], rc[M], rd[M];
     long_load<T, M>(a, b, c, d, L, base, i0, vec_ok, ra, rb, rc, rd);
@@ -311,6 +323,9 @@ static trid_status solve_lines(const T *a, const T *b, const T *c, const T *d, T
     const size_t one = align_up(size_t(L.nsys) * size_t(R) * sizeof(T), 256);
     if (ws_bytes < long_ws_bytes<T>(L.nsys, L.n) || ws == nullptr) return TRID_ERR_ALLOC;
     if (!contig && (ntiles + 7) / 8 > 65535) return TRID_ERR_UNSUPPORTED;  // grid.y limit
+    // the kernels' 32-bit thread and line indices
+    if (L.nsys * ntiles >= (int64_t(1) << 31) || L.nsys >= (int64_t(1) << 31))
+        return TRID_ERR_UNSUPPORTED;
     T *ra = reinterpret_cast<T *>(ws);
     T *rc = reinterpret_cast<T *>(ws + one);
     T *rd = reinterpret_cast<T *>(ws + 2 * one);
