@@ -302,20 +302,64 @@ __device__ __forceinline__ void store_sys_tile(T *out, int accumulate, int64_t s
     }
 }
 
-// Reduce `lv[0]` (rows R of level 0 already written) level by level until one
-// warp can solve the top level, solve it, and substitute back down to level 0
-// (whose solution is then in lv[0].d).  All threads of the block call it.
+// Parallel cyclic reduction (Algorithm "pcr") of one unit-diagonal level held
+// in shared memory, by the whole block: the calling thread owns rows tid and
+// tid + blockDim.x (R <= 2 blockDim.x).  Each round reads the neighbours it
+// needs into registers, waits for the block, then writes.  On a diagonally
+// dominant system every round squares the coupling coefficients; once all of
+// them are below 2^-(p+4) (p the significand bits) the remaining rounds change
+// no value by more than 1/16 ulp, and the level's d holds the solution.
+template <typename T>
+__device__ void block_pcr(RLevel<T> &lv) {
+    constexpr float negligible = sizeof(T) == 4 ? 3.7252903e-09f : 6.9388939e-18f;
+    const int R = lv.R, nth = blockDim.x, tid = threadIdx.x;
+    float cpl = 0.0f;
+    for (int i = tid; i < R; i += nth)
+        cpl = fmaxf(cpl, float(fmax(fabs(lv.a[i]), fabs(lv.c[i]))));
+    if (!__syncthreads_or(cpl >= negligible)) return;
+    for (int s = 1; s < R; s <<= 1) {
+        T na[2], nc[2], nd[2];
+        float cmax = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = tid + q * nth;
+            na[q] = nc[q] = nd[q] = T(0);
+            if (i < R) {
+                const T ai = lv.a[i], ci = lv.c[i], di = lv.d[i];
+                T am = T(0), cm = T(0), dm = T(0), ap = T(0), cp = T(0), dp = T(0);
+                if (i - s >= 0) { am = lv.a[i - s]; cm = lv.c[i - s]; dm = lv.d[i - s]; }
+                if (i + s < R) { ap = lv.a[i + s]; cp = lv.c[i + s]; dp = lv.d[i + s]; }
+                const T r = rcp(T(1) - ai * cm - ci * ap);
+                na[q] = -r * (ai * am);
+                nc[q] = -r * (ci * cp);
+                nd[q] = r * (di - ai * dm - ci * dp);
+                cmax = fmaxf(cmax, float(fmax(fabs(na[q]), fabs(nc[q]))));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = tid + q * nth;
+            if (i < R) { lv.a[i] = na[q]; lv.c[i] = nc[q]; lv.d[i] = nd[q]; }
+        }
+        if (!__syncthreads_or(cmax >= negligible)) break;
+    }
+}
+
+// Solve the reduced system held in level 0 (rows R already written, block
+// synchronised): tile passes in shared memory while it is longer than two rows
+// per thread, the block PCR on the top level, then substitution back down to
+// level 0 (whose solution is then in lv[0].d).  All threads of the block call it.
 template <typename T>
 __device__ void block_reduced_solve(RLevel<T> *lv, int nlevels) {
-    const int warp = threadIdx.x >> 5;
     int top = 0;
-    while (lv[top].R > VL_SHORT && top + 1 < nlevels) {
+    while (lv[top].R > 2 * int(blockDim.x) && top + 1 < nlevels) {
         lv[top + 1].R = 2 * ((lv[top].R + VL_M - 1) / VL_M);
         level_reduce<T>(lv[top], lv[top + 1]);
         __syncthreads();
         ++top;
     }
-    if (warp == 0) level_warp_solve<T>(lv[top]);
+    block_pcr<T>(lv[top]);
     __syncthreads();
     for (int l = top - 1; l >= 0; --l) {
         level_substitute<T>(lv[l], lv[l + 1]);
