@@ -225,6 +225,17 @@ size_t adi_workspace_bytes(const int64_t *dims, int ndim, trid_dtype dtype);
  */
 trid_status trid_get_device_status(trid_stream_t stream);
 
+/*
+ * Bounded wait on a device flag (diagnostic; not in the paper): one thread
+ * waits on `stream` until the device int *flag equals `expect` or timeout_s
+ * seconds (0 < timeout_s <= 1) of device time have passed; on expiry it
+ * records TRID_ERR_TIMEOUT in the device status word and returns, the same
+ * way the TMA-fed kernels give up on an mbarrier.  Lets a caller check the
+ * bounded-wait path without a hang or a fault.  Errors: TRID_ERR_INVALID_ARG
+ * (NULL flag, timeout outside (0, 1]), TRID_ERR_MISALIGNED, TRID_ERR_CUDA.
+ */
+trid_status trid_wait_flag(const int *flag, int expect, double timeout_s, trid_stream_t stream);
+
 /* Library version string (static storage). */
 /*
  * Length classes of trid_solve_batch_varlen: systems of up to 248 rows are

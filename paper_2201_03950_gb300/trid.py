@@ -75,6 +75,7 @@ def _bind(L):
         "adi2v_forward": ([P, P, P, P, f64, i32, i32, P, sz, i32, P, sz, P], i32),
         "adi2v_backward": ([P, P, P, P, P, P, f64, i32, i32, P, sz, i32, P, sz, P], i32),
         "trid_get_device_status": ([P], i32),
+        "trid_wait_flag": ([P, i32, f64, P], i32),
         "trid_status_string": ([i32], ctypes.c_char_p),
         "trid_last_cuda_error": ([], ctypes.c_char_p),
         "trid_version": ([], ctypes.c_char_p),
@@ -368,6 +369,18 @@ def adi2v_backward(g_uT, kappa, dims, lam: float, nsteps: int, every: int, ckpt,
     if st != 0:
         raise TridError(st, "adi2v_backward")
     return g_u0, g_k, g_coef
+
+
+def wait_flag(flag, expect: int, timeout_s: float, stream=None):
+    """Bounded device wait until the int32 CUDA tensor ``flag`` equals
+    ``expect``; on expiry TRID_ERR_TIMEOUT is recorded in the device status
+    word (read it with ``device_status``)."""
+    import torch
+    if not (flag.is_cuda and flag.dtype == torch.int32 and flag.numel() >= 1):
+        raise ValueError("flag must be an int32 CUDA tensor")
+    st = load().trid_wait_flag(_ptr(flag), int(expect), float(timeout_s), _stream(stream))
+    if st != 0:
+        raise TridError(st, "trid_wait_flag")
 
 
 def device_status(stream=None) -> int:

@@ -1,0 +1,78 @@
+"""Failure detection without a device fault: host-side argument faults on
+every entry point (no GPU needed), and the bounded device wait that records
+TRID_ERR_TIMEOUT in the status word instead of hanging (GPU)."""
+import ctypes
+import time
+
+import pytest
+
+from paper_2201_03950_gb300 import trid
+
+TIMEOUT = 6
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_03950_gb300 import build
+    build.build()
+    return trid.load()
+
+
+def _dims(*v):
+    return (ctypes.c_int64 * len(v))(*v)
+
+
+def test_host_side_faults_return_codes_without_launching(lib):
+    p = ctypes.c_void_p(4096)
+    # bounded-wait diagnostic: NULL flag, timeout outside (0, 1], misaligned flag
+    assert lib.trid_wait_flag(None, 1, 0.1, None) == 1
+    assert lib.trid_wait_flag(p, 1, 0.0, None) == 1
+    assert lib.trid_wait_flag(p, 1, 2.0, None) == 1
+    assert lib.trid_wait_flag(ctypes.c_void_p(4097), 1, 0.1, None) == 3
+    # batched ADI: bad dims, lambda, nsteps
+    assert lib.adi_step_batched(p, 1, _dims(8, 2), 2, 0.1, 1, 0, None, 0, None) == 1
+    assert lib.adi_step_batched(p, 1, _dims(8, 8), 2, -1.0, 1, 0, None, 0, None) == 1
+    assert lib.adi_step_batched(p, 1, _dims(8, 8), 2, 0.1, -1, 0, None, 0, None) == 1
+    assert lib.adi_step_batched(p, -1, _dims(8, 8), 2, 0.1, 1, 0, None, 0, None) == 1
+    # differentiable ADI: every < 1, lambda <= 0, workspace missing
+    assert lib.adi2v_forward(p, p, p, _dims(8, 8), 0.1, 3, 0, None, 0, 0, p, 1 << 20, None) == 1
+    assert lib.adi2v_forward(p, p, p, _dims(8, 8), -0.1, 3, 2, None, 0, 0, p, 1 << 20, None) == 1
+    assert lib.adi2v_forward(p, p, p, _dims(8, 8), 0.1, 3, 2, None, 0, 0, None, 0, None) == 5
+    # uneven batch: a class split that is not one of the admissible ones
+    cfg = trid.VarlenConfig(300, 4088)
+    assert lib.trid_solve_batch_varlen_cfg(p, p, p, p, None, p, 1, 8, 8, 0, p, 1 << 20, None,
+                                           ctypes.byref(cfg)) == 1
+
+
+@pytest.mark.gpu
+def test_bounded_wait_expires_and_is_reported():
+    torch = pytest.importorskip("torch")
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert trid.device_status() == 0
+    t0 = time.time()
+    trid.wait_flag(flag, 1, 0.2)          # nothing ever sets the flag
+    assert trid.device_status() == TIMEOUT  # synchronises, reads and clears
+    assert time.time() - t0 < 30
+    assert trid.device_status() == 0      # cleared by the read
+
+
+@pytest.mark.gpu
+def test_bounded_wait_returns_when_the_flag_is_set_and_context_stays_usable():
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    from paper_2201_03950_gb300 import inputs
+    import oracle
+    flag = torch.ones(1, dtype=torch.int32, device="cuda")
+    trid.wait_flag(flag, 1, 0.5)
+    assert trid.device_status() == 0
+    # after an expired wait the context still runs the solver correctly
+    trid.wait_flag(torch.zeros(1, dtype=torch.int32, device="cuda"), 7, 0.05)
+    assert trid.device_status() == TIMEOUT
+    dims = (64, 32)
+    a, b, c, d = inputs.dominant_system((2048,), seed=3, dtype=np.float32)
+    ref = oracle.solve_mesh(a, b, c, d, dims, 1)
+    ta, tb, tc, td = (torch.from_numpy(v).cuda() for v in (a, b, c, d))
+    trid.solve(ta, tb, tc, td, dims, 1)
+    got = td.cpu().numpy()
+    assert float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))) <= 1e-5
+    assert trid.device_status() == 0
