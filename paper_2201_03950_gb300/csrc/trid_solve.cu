@@ -20,8 +20,12 @@
 //             systems (2 rows per tile) are solved by a recursive call, and
 //             k_long_subst recomputes each tile and substitutes the tile-end
 //             unknowns back.
+//  k_lines_tma  contiguous FP32 systems of 256 < N <= 4096 in one pass:
+//             whole systems staged in shared memory by bulk copies, one team
+//             of warps per system (trid_lines_tma.cuh).
 #include "trid_device.cuh"
 #include "trid_strided.cuh"
+#include "trid_lines_tma.cuh"
 #include "../../include/trid.h"
 #include "trid_internal.h"
 
@@ -285,6 +289,51 @@ static void launch_strided(const T *a, const T *b, const T *c, const T *d, T *ou
             <<<strided_grid(L, SG), NT * SG, 0, st>>>(coef, d, out, L, L.nsys / L.inner);
 }
 
+// Contiguous FP32 systems of 256 < n <= 4096 through k_lines_tma with teams
+// of TW warps (n <= 256 * TW).  False, having launched nothing, when the
+// shared memory does not fit.
+template <int TW>
+static bool launch_lines_tma_tw(const float *a, const float *b, const float *c, const float *d,
+                                float *out, int acc, const Lines &L, cudaStream_t st) {
+    using LY = LinesTmaLayout<float, TW>;
+    const DeviceInfo *di = device_info();
+    if (!di) return false;
+    const int n = int(L.n);
+    const int narr = b ? 4 : 3;
+    int stages = 6;
+    while (stages > 2 && LY::bytes(n, narr, stages) > size_t(di->max_smem_optin)) --stages;
+    const size_t smem = LY::bytes(n, narr, stages);
+    if (smem > size_t(di->max_smem_optin)) return false;
+    auto kern = k_lines_tma<float, TW>;
+    const int per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), LT_CONS + 32, smem);
+    if (per_sm < 1) return false;
+    const int64_t nbatch = (L.nsys + LY::NTEAM - 1) / LY::NTEAM;
+    const int64_t slots = int64_t(di->sm_count) * per_sm;
+    const int64_t grid = nbatch < slots ? nbatch : slots;
+    kern<<<dim3(unsigned(grid)), LT_CONS + 32, smem, st>>>(a, b, c, d, out, acc, int(L.nsys), n,
+                                                           int(nbatch), stages,
+                                                           device_status_word());
+    return cudaGetLastError() == cudaSuccess;
+}
+
+template <typename T>
+static bool launch_lines_tma(const T *a, const T *b, const T *c, const T *d, T *out, int acc,
+                             const Lines &L, cudaStream_t st) {
+    if constexpr (!std::is_same<T, float>::value) {
+        return false;
+    } else {
+        const bool aligned = is_aligned16(a) && is_aligned16(c) && is_aligned16(d) &&
+                             is_aligned16(out) && (!b || is_aligned16(b));
+        if (L.stride != 1 || !aligned || L.n % 4 != 0 || L.n <= MAX_SINGLE_PASS ||
+            L.n > LT_MAX_N || L.nsys >= (int64_t(1) << 31) || L.nsys * L.n >= (int64_t(1) << 40))
+            return false;
+        if (L.n <= 512) return launch_lines_tma_tw<2>(a, b, c, d, out, acc, L, st);
+        if (L.n <= 1024) return launch_lines_tma_tw<4>(a, b, c, d, out, acc, L, st);
+        if (L.n <= 2048) return launch_lines_tma_tw<8>(a, b, c, d, out, acc, L, st);
+        return launch_lines_tma_tw<16>(a, b, c, d, out, acc, L, st);
+    }
+}
+
 template <typename T>
 static trid_status solve_lines(const T *a, const T *b, const T *c, const T *d, T *out, int acc,
                                const Lines &L, char *ws, size_t ws_bytes, cudaStream_t st) {
@@ -317,6 +366,8 @@ static trid_status solve_lines(const T *a, const T *b, const T *c, const T *d, T
         }
         return cudaGetLastError() == cudaSuccess ? TRID_OK : TRID_ERR_CUDA;
     }
+    // up to 4096 contiguous FP32 rows: one pass, systems staged by bulk copies
+    if (launch_lines_tma<T>(a, b, c, d, out, acc, L, st)) return TRID_OK;
     // long systems: tiled Thomas-PCR in passes
     const int64_t ntiles = (L.n + TILE_M - 1) / TILE_M;
     const int64_t R = 2 * ntiles;
