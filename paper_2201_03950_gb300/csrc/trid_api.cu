@@ -57,6 +57,59 @@ OccEntry g_occ[kOccCache];
 int g_nocc = 0;
 }  // namespace
 
+namespace {
+struct ClusterEntry {
+    const void *kernel;
+    int dev, csize, threads;
+    size_t smem;
+    int clusters;
+};
+constexpr int kClusterCache = 64;
+ClusterEntry g_ccache[kClusterCache];
+int g_ncc = 0;
+}  // namespace
+
+int cluster_capacity(const void *kernel, int csize, int threads, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int i = 0; i < g_ncc; ++i) {
+        const ClusterEntry &e = g_ccache[i];
+        if (e.kernel == kernel && e.dev == dev && e.csize == csize && e.threads == threads &&
+            e.smem == smem)
+            return e.clusters;
+    }
+    if (csize > 8) {
+        const cudaError_t ae =
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (ae != cudaSuccess) {
+            cudaGetLastError();
+            note_cuda_error(ae);
+            return 0;
+        }
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(csize);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(unsigned(csize));
+    cfg.blockDim = dim3(unsigned(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t oe = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg);
+    if (oe != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    if (g_ncc < kClusterCache)
+        g_ccache[g_ncc++] = ClusterEntry{kernel, dev, csize, threads, smem, n};
+    return n;
+}
+
 int kernel_blocks_per_sm(const void *kernel, int threads, size_t smem) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -92,7 +145,7 @@ int kernel_blocks_per_sm(const void *kernel, int threads, size_t smem) {
 }
 
 bool encode_lines_map(void *map, const void *base, int esz, int64_t inner, int64_t n,
-                      int64_t outer, int box_x) {
+                      int64_t outer, int box_x, int box_rows) {
     {
         std::lock_guard<std::mutex> lk(g_pool_mu);
         if (!g_encode_tried) {
@@ -109,12 +162,14 @@ bool encode_lines_map(void *map, const void *base, int esz, int64_t inner, int64
     }
     if (!g_encode) return false;
     if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
-    if ((inner * esz) % 16 != 0 || n < 1 || n > 256 || inner < 1 || outer < 1) return false;
-    if (inner >= (int64_t(1) << 32) || outer >= (int64_t(1) << 31)) return false;
+    const int64_t rows = box_rows > 0 ? box_rows : n;
+    if ((inner * esz) % 16 != 0 || n < 1 || rows > 256 || inner < 1 || outer < 1) return false;
+    if (inner >= (int64_t(1) << 32) || outer >= (int64_t(1) << 31) || n >= (int64_t(1) << 32))
+        return false;
     const cuuint64_t dims[3] = {cuuint64_t(inner), cuuint64_t(n), cuuint64_t(outer)};
     const cuuint64_t strides[2] = {cuuint64_t(inner * esz), cuuint64_t(inner * n * esz)};
     if (strides[1] >= (cuuint64_t(1) << 40)) return false;
-    const cuuint32_t box[3] = {cuuint32_t(box_x), cuuint32_t(n), 1};
+    const cuuint32_t box[3] = {cuuint32_t(box_x), cuuint32_t(rows), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = g_encode(
         static_cast<CUtensorMap *>(map),

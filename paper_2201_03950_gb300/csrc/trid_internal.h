@@ -26,9 +26,14 @@ struct DeviceInfo {
 const DeviceInfo *device_info();
 
 // 3D tensor map over a strided line set viewed as (inner, n, outer) with the
-// box (box_x, n, 1); false if the TMA constraints do not hold.
+// box (box_x, box_rows, 1) (box_rows = 0: all n rows, n <= 256); false if the
+// TMA constraints do not hold.
 bool encode_lines_map(void *map /* CUtensorMap */, const void *base, int esz, int64_t inner,
-                      int64_t n, int64_t outer, int box_x);
+                      int64_t n, int64_t outer, int box_x, int box_rows = 0);
+
+// Clusters of `csize` CTAs of `kernel` that can be resident at once (0 if
+// none or the query fails); sizes above 8 are enabled on the function first.
+int cluster_capacity(const void *kernel, int csize, int threads, size_t smem);
 
 // Blocks of `kernel` resident per SM for (threads, dynamic smem) on the
 // current device, after raising the kernel's dynamic shared-memory limit to

@@ -7,8 +7,8 @@
 // batch: a batch is one contiguous range of every array), completion counted
 // on mbarriers; it runs up to `stages` batches ahead, so HBM keeps streaming
 // while the consumers solve.  The consumers form teams of TW warps, one system
-// per team: every thread owns M = 8 consecutive rows (tile_reduce in
-// registers), the team's 2 * ntiles reduced rows go to shared memory and are
+// per team: every thread owns M = 8 (16 for N > 2048) consecutive rows
+// (tile_reduce in registers), the team's 2 * ntiles reduced rows go to shared memory and are
 // solved there by parallel cyclic reduction (Algorithm "pcr") with named
 // barriers, stopping as soon as every coupling coefficient is below 1/16 ulp
 // (the later rounds would change no value by more than that), and every
@@ -20,9 +20,8 @@
 
 namespace trid {
 
-constexpr int LT_M = 8;           // rows per thread
 constexpr int LT_CONS = 512;      // consumer threads (16 warps)
-constexpr int LT_MAX_N = LT_CONS * LT_M;
+constexpr int LT_MAX_N = 4096;    // longest system (8 warps x 32 lanes x 16 rows)
 
 // 1D bulk copy global -> shared, completion counted on `bar` (both addresses
 // and the size multiples of 16 bytes).
@@ -94,14 +93,15 @@ __device__ __forceinline__ void team_pcr(T *A, T *C, T *D, int R, int t, int nth
 }
 
 // Shared-memory layout of k_lines_tma: `stages` stages of narr slots (one per
-// array), each slot NTEAM * n elements; then two buffers of reduced rows
-// (A, C, D per team); then the full/empty mbarriers.
-template <typename T, int TW>
+// array), each slot SPS * n elements (SPS systems per stage); then two
+// buffers of reduced rows (A, C, D per team); then the full/empty mbarriers.
+template <typename T, int TW, int SPS>
 struct LinesTmaLayout {
     static constexpr int TT = 32 * TW;               // threads per team
-    static constexpr int NTEAM = LT_CONS / TT;       // systems per batch
+    static constexpr int NTEAM = LT_CONS / TT;       // teams per block
+    static_assert(NTEAM % SPS == 0, "teams split evenly over the systems of a stage");
     __host__ __device__ static size_t slot_bytes(int n) {
-        return (size_t(NTEAM) * n * sizeof(T) + 127) / 128 * 128;
+        return (size_t(SPS) * n * sizeof(T) + 127) / 128 * 128;
     }
     __host__ __device__ static size_t red_bytes() {
         return 2 * size_t(NTEAM) * 3 * 2 * TT * sizeof(T);
@@ -112,17 +112,19 @@ struct LinesTmaLayout {
 };
 
 // nsys systems of n rows, system s at [s * n, s * n + n) of every array;
-// b == nullptr means a unit diagonal.  Requirements (host): every pointer 16-byte
-// aligned, n % 4 == 0 (FP32), 8 * 32 * TW / 2 < n <= 8 * 32 * TW.
-template <typename T, int TW>
+// b == nullptr means a unit diagonal.  M rows per thread; a stage holds SPS
+// systems, and the NTEAM / SPS groups of SPS teams take the stages in turn.
+// Requirements (host): every pointer 16-byte aligned, n % 4 == 0 (FP32),
+// n <= M * 32 * TW.
+template <typename T, int TW, int M, int SPS>
 __global__ void __launch_bounds__(LT_CONS + 32, 1)
 k_lines_tma(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c,
             const T *d, T *out, int accumulate, int nsys, int n, int nbatch, int stages,
             int *status) {
-    using LY = LinesTmaLayout<T, TW>;
+    using LY = LinesTmaLayout<T, TW, SPS>;
     constexpr int TT = LY::TT;
     constexpr int NTEAM = LY::NTEAM;
-    constexpr int M = LT_M;
+    constexpr int NG = NTEAM / SPS;  // team groups, taking stages in turn
     extern __shared__ __align__(128) unsigned char smem[];
     const int narr = b ? 4 : 3;
     const size_t slot = LY::slot_bytes(n);
@@ -137,7 +139,7 @@ k_lines_tma(const T *__restrict__ a, const T *__restrict__ b, const T *__restric
         abort_flag = 0;
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], LT_CONS / 32);
+            mbar_init(&empty[s], SPS * TW);  // the warps of one team group
         }
         fence_mbar_init();
     }
@@ -155,8 +157,8 @@ k_lines_tma(const T *__restrict__ a, const T *__restrict__ b, const T *__restric
                     *(volatile int *)&abort_flag = 1;
                     break;
                 }
-                const int sys0 = bt * NTEAM;
-                const int cnt = nsys - sys0 < NTEAM ? nsys - sys0 : NTEAM;
+                const int sys0 = bt * SPS;
+                const int cnt = nsys - sys0 < SPS ? nsys - sys0 : SPS;
                 const uint32_t bytes = uint32_t(cnt) * uint32_t(n) * uint32_t(sizeof(T));
                 mbar_expect_tx(&full[s], uint32_t(narr) * bytes);
                 unsigned char *dst = smem + s * stage_bytes;
@@ -170,23 +172,25 @@ k_lines_tma(const T *__restrict__ a, const T *__restrict__ b, const T *__restric
 
     const int lane = tid & 31;
     const int team = tid / TT, t = tid % TT;
+    const int tg = team / SPS, ts = team % SPS;  // team group, system of the stage
     const int bar = 1 + team;  // named barrier of the team (0 is __syncthreads)
     const int i0 = t * M;
     const int ntiles = (n + M - 1) / M;
     const bool mine = t < ntiles;
     const bool full_tile = i0 + M <= n;
-    int k = 0;
-    for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x, ++k) {
+    int kk = 0;  // this team's own batch count
+    for (int k = tg, bt = blockIdx.x + tg * gridDim.x; bt < nbatch;
+         k += NG, bt += NG * gridDim.x, ++kk) {
         const int s = k % stages;
         bool ok = false;
         if (!*(volatile int *)&abort_flag) {
             ok = mbar_wait(&full[s], uint32_t(k / stages) & 1u, status);
             if (!ok) *(volatile int *)&abort_flag = 1;
         }
-        const int sys = bt * NTEAM + team;
+        const int sys = bt * SPS + ts;
         const bool active = ok && sys < nsys;  // uniform over the team
         const unsigned char *stg = smem + s * stage_bytes;
-        const size_t row0 = size_t(team) * n + i0;
+        const size_t row0 = size_t(ts) * n + i0;
         const T *sa = reinterpret_cast<const T *>(stg) + row0;
         const T *sc = reinterpret_cast<const T *>(stg + slot) + row0;
         const T *sd = reinterpret_cast<const T *>(stg + 2 * slot) + row0;
@@ -222,8 +226,8 @@ k_lines_tma(const T *__restrict__ a, const T *__restrict__ b, const T *__restric
         }
         T as, cs, ds, ae, ce, de;
         tile_reduce<T, M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-        // reduced rows: buffer k & 1 (the previous system's stays readable)
-        T *RA = red + (size_t((k & 1) * NTEAM + team) * 3) * (2 * TT);
+        // reduced rows: buffer kk & 1 (the previous system's stays readable)
+        T *RA = red + (size_t((kk & 1) * NTEAM + team) * 3) * (2 * TT);
         T *RC = RA + 2 * TT, *RD = RA + 4 * TT;
         if (mine) {
             RA[2 * t] = as; RC[2 * t] = cs; RD[2 * t] = ds;

@@ -23,9 +23,13 @@
 //  k_lines_tma  contiguous FP32 systems of 256 < N <= 4096 in one pass:
 //             whole systems staged in shared memory by bulk copies, one team
 //             of warps per system (trid_lines_tma.cuh).
+//  k_chunk_cluster  strided FP32 systems of 256 < N <= 4096 in one pass:
+//             chunks of 256 rows, one CTA each, joined by a chunk-level solve
+//             across a thread-block cluster (trid_chunked.cuh).
 #include "trid_device.cuh"
 #include "trid_strided.cuh"
 #include "trid_lines_tma.cuh"
+#include "trid_chunked.cuh"
 #include "../../include/trid.h"
 #include "trid_internal.h"
 
@@ -290,12 +294,12 @@ static void launch_strided(const T *a, const T *b, const T *c, const T *d, T *ou
 }
 
 // Contiguous FP32 systems of 256 < n <= 4096 through k_lines_tma with teams
-// of TW warps (n <= 256 * TW).  False, having launched nothing, when the
+// of TW warps, M rows per thread (n <= 32 * TW * M).  False, having launched nothing, when the
 // shared memory does not fit.
-template <int TW>
+template <int TW, int M, int SPS>
 static bool launch_lines_tma_tw(const float *a, const float *b, const float *c, const float *d,
                                 float *out, int acc, const Lines &L, cudaStream_t st) {
-    using LY = LinesTmaLayout<float, TW>;
+    using LY = LinesTmaLayout<float, TW, SPS>;
     const DeviceInfo *di = device_info();
     if (!di) return false;
     const int n = int(L.n);
@@ -304,10 +308,10 @@ static bool launch_lines_tma_tw(const float *a, const float *b, const float *c, 
     while (stages > 2 && LY::bytes(n, narr, stages) > size_t(di->max_smem_optin)) --stages;
     const size_t smem = LY::bytes(n, narr, stages);
     if (smem > size_t(di->max_smem_optin)) return false;
-    auto kern = k_lines_tma<float, TW>;
+    auto kern = k_lines_tma<float, TW, M, SPS>;
     const int per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), LT_CONS + 32, smem);
     if (per_sm < 1) return false;
-    const int64_t nbatch = (L.nsys + LY::NTEAM - 1) / LY::NTEAM;
+    const int64_t nbatch = (L.nsys + SPS - 1) / SPS;
     const int64_t slots = int64_t(di->sm_count) * per_sm;
     const int64_t grid = nbatch < slots ? nbatch : slots;
     kern<<<dim3(unsigned(grid)), LT_CONS + 32, smem, st>>>(a, b, c, d, out, acc, int(L.nsys), n,
@@ -327,10 +331,66 @@ static bool launch_lines_tma(const T *a, const T *b, const T *c, const T *d, T *
         if (L.stride != 1 || !aligned || L.n % 4 != 0 || L.n <= MAX_SINGLE_PASS ||
             L.n > LT_MAX_N || L.nsys >= (int64_t(1) << 31) || L.nsys * L.n >= (int64_t(1) << 40))
             return false;
-        if (L.n <= 512) return launch_lines_tma_tw<2>(a, b, c, d, out, acc, L, st);
-        if (L.n <= 1024) return launch_lines_tma_tw<4>(a, b, c, d, out, acc, L, st);
-        if (L.n <= 2048) return launch_lines_tma_tw<8>(a, b, c, d, out, acc, L, st);
-        return launch_lines_tma_tw<16>(a, b, c, d, out, acc, L, st);
+        if (L.n <= 512) return launch_lines_tma_tw<2, 8, 8>(a, b, c, d, out, acc, L, st);
+        if (L.n <= 1024) return launch_lines_tma_tw<4, 8, 4>(a, b, c, d, out, acc, L, st);
+        if (L.n <= 2048) return launch_lines_tma_tw<8, 8, 2>(a, b, c, d, out, acc, L, st);
+        // two teams of 8 warps, 16 rows per thread, taking one-system stages
+        // in turn: two systems in flight
+        return launch_lines_tma_tw<8, 16, 1>(a, b, c, d, out, acc, L, st);
+    }
+}
+
+// Strided FP32 systems of 256 < n <= 4096 rows through k_chunk_cluster: one
+// cluster of C = ceil(n / 256) CTAs per strip of 16 systems, as many clusters
+// as can be resident.  False, having launched nothing, when a constraint
+// (TMA alignment, 32-bit indexing, cluster scheduling) does not hold.
+template <typename T>
+static bool launch_chunk_cluster(const T *a, const T *b, const T *c, const T *d, T *out, int acc,
+                                 const Lines &L, cudaStream_t st) {
+    if constexpr (!std::is_same<T, float>::value) {
+        return false;
+    } else {
+        if (L.stride == 1 || !b || L.n <= MAX_SINGLE_PASS ||
+            L.n > int64_t(CK_ROWS) * CK_MAX_CHUNKS || !strided_offsets_fit(L))
+            return false;
+        const int C = int((L.n + CK_ROWS - 1) / CK_ROWS);
+        const int64_t outer = L.nsys / L.inner;
+        const int64_t nxc = (L.inner + CK_SG - 1) / CK_SG;
+        const int64_t nstrips = nxc * outer;
+        if (nstrips >= (int64_t(1) << 31) || L.inner >= (int64_t(1) << 31)) return false;
+        TmaSet maps;
+        const void *arrs[4] = {a, b, c, d};
+        for (int q = 0; q < 4; ++q)
+            if (!encode_lines_map(&maps.map[q], arrs[q], int(sizeof(T)), L.inner, L.n, outer,
+                                  CK_SG, CK_ROWS))
+                return false;
+        const size_t smem = ChunkLayout<T>::bytes(C);
+        auto kern = k_chunk_cluster<T>;
+        const void *kp = reinterpret_cast<const void *>(kern);
+        if (kernel_blocks_per_sm(kp, CK_THREADS, smem) < 1) return false;
+        const int ncl_max = cluster_capacity(kp, C, CK_THREADS, smem);
+        if (ncl_max < 1) return false;
+        const int64_t ncl = nstrips < ncl_max ? nstrips : ncl_max;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = unsigned(C);
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(unsigned(C * ncl));
+        cfg.blockDim = dim3(CK_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, out, acc, L, int(nstrips),
+                                                 device_status_word());
+        if (e != cudaSuccess) {
+            note_cuda_error(e);
+            cudaGetLastError();
+            return false;
+        }
+        return true;
     }
 }
 
@@ -368,6 +428,8 @@ static trid_status solve_lines(const T *a, const T *b, const T *c, const T *d, T
     }
     // up to 4096 contiguous FP32 rows: one pass, systems staged by bulk copies
     if (launch_lines_tma<T>(a, b, c, d, out, acc, L, st)) return TRID_OK;
+    // strided FP32 up to 4096 rows: one cluster per strip of systems
+    if (launch_chunk_cluster<T>(a, b, c, d, out, acc, L, st)) return TRID_OK;
     // long systems: tiled Thomas-PCR in passes
     const int64_t ntiles = (L.n + TILE_M - 1) / TILE_M;
     const int64_t R = 2 * ntiles;
