@@ -85,8 +85,13 @@ k_adi_xy(const T *__restrict__ u, T *__restrict__ e, T *__restrict__ rs, T *__re
             const int y = t * YM + r;
             const bool rowint = act && zint && y > 0 && y < ny - 1;
             const T *row = ut + r * nx;
-            T uc[M], zs[M], d[M], zu[M];
+            T uc[M], zs[M], d[M], zu[M], ym[M], yp[M];
+            // all five lines' loads in flight together (one round trip): the
+            // y neighbours of a boundary row are read from the row itself and
+            // not used
             load_line_tile<T, M>(row, x0, nx, act, uc);
+            load_line_tile<T, M>(rowint ? row - nx : row, x0, nx, act, ym);
+            load_line_tile<T, M>(rowint ? row + nx : row, x0, nx, act, yp);
             {
                 T zm[M], zp[M];
                 load_line_tile<T, M>(row - plane, x0, nx, act && zint, zm);
@@ -99,9 +104,6 @@ k_adi_xy(const T *__restrict__ u, T *__restrict__ e, T *__restrict__ rs, T *__re
             const T left = __shfl_up_sync(FULL, uc[M - 1], 1, G);
             const T right = __shfl_down_sync(FULL, uc[0], 1, G);
             if (rowint) {
-                T ym[M], yp[M];
-                load_line_tile<T, M>(row - nx, x0, nx, true, ym);
-                load_line_tile<T, M>(row + nx, x0, nx, true, yp);
 #pragma unroll
                 for (int j = 0; j < M; ++j) {
                     const T xm = (j == 0) ? left : uc[j - 1];
