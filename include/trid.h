@@ -147,7 +147,9 @@ size_t trid_adjoint_workspace_bytes(const int64_t *dims, int ndim, int solve_dim
  *   max_len    host: an upper bound of the system lengths; it sizes the
  *              shared-memory reduced systems (TRID_ERR_UNSUPPORTED when they
  *              do not fit: about 56K rows in FP32, 28K in FP64).
- *   u, dtype, stream  as for trid_solve_batch (u == NULL: in place in d).
+ *   u, dtype, stream  as for trid_solve_batch (u == NULL: in place in d),
+ *              except that a, b, c, d and u must start on 16-byte boundaries
+ *              (TRID_ERR_MISALIGNED otherwise, nothing launched).
  *   workspace  caller device scratch of trid_solve_varlen_workspace_bytes(nsys)
  *              bytes, 256-byte aligned (work order and queue counters; fully
  *              rewritten by every call, so calls on one workspace must not

@@ -666,8 +666,9 @@ static trid_status varlen_entry(const void *a, const void *b, const void *c, voi
     if (!a || !b || !c || !d || !offsets) return TRID_ERR_INVALID_ARG;
     const size_t esz = dtype == TRID_F32 ? 4 : 8;
     const void *ptrs[5] = {a, b, c, d, u};
+    // the kernels read 16-byte tiles aligned to the arrays' bases
     for (int k = 0; k < 5; ++k)
-        if (ptrs[k] && (reinterpret_cast<uintptr_t>(ptrs[k]) % esz) != 0) return TRID_ERR_MISALIGNED;
+        if (ptrs[k] && (reinterpret_cast<uintptr_t>(ptrs[k]) % 16) != 0) return TRID_ERR_MISALIGNED;
     if (reinterpret_cast<uintptr_t>(offsets) % 8 != 0) return TRID_ERR_MISALIGNED;
     if (u) {
         const char *pu = static_cast<const char *>(u);

@@ -42,6 +42,11 @@ def test_host_side_faults_return_codes_without_launching(lib):
     cfg = trid.VarlenConfig(300, 4088)
     assert lib.trid_solve_batch_varlen_cfg(p, p, p, p, None, p, 1, 8, 8, 0, p, 1 << 20, None,
                                            ctypes.byref(cfg)) == 1
+    # uneven batch: arrays 4-byte but not 16-byte aligned are rejected before
+    # any launch (the kernels read 16-byte tiles aligned to the bases)
+    q = ctypes.c_void_p(4096 + 4)
+    for args in ((q, p, p, p, None), (p, p, p, q, None), (p, p, p, p, q)):
+        assert lib.trid_solve_batch_varlen(*args, p, 1, 8, 8, 0, p, 1 << 20, None) == 3
 
 
 @pytest.mark.gpu
