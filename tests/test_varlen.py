@@ -71,6 +71,21 @@ def test_varlen_loguniform(dtype):
     assert per_system_err(got, ref, off) <= TOL[dtype]
 
 
+def test_varlen_long_class_alignments_and_ragged_end():
+    """FP32 systems longer than 4088 rows (the two-pass class) at every start
+    alignment (1-3 rows of tile padding), the last system ending in the
+    arrays' ragged last 16 bytes (total % 4 == 1), accumulate mode; against
+    the oracle, and with a larger max_len (deeper shared-memory levels)."""
+    lengths = [3, 17404, 4089, 5000, 1, 8191, 2, 12345, 16384, 7, 4090, 17401]
+    assert sum(lengths) % 4 == 1
+    got, ref, off = run(lengths, np.float32, seed=21)
+    assert per_system_err(got, ref, off) <= TOL[np.float32]
+    got2, _, _ = run(lengths, np.float32, seed=21, max_len=30000)
+    assert per_system_err(got2, ref, off) <= TOL[np.float32]
+    gacc, racc, _ = run(lengths, np.float32, seed=22, accumulate=True)
+    assert per_system_err(gacc, racc, off) <= TOL[np.float32]
+
+
 def test_varlen_accumulate_and_many_short():
     lengths = np.concatenate([np.full(3000, 17), [4096, 300], np.arange(1, 60)])
     got, ref, off = run(lengths, np.float32, seed=3, accumulate=True)
