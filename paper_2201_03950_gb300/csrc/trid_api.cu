@@ -144,23 +144,26 @@ int kernel_blocks_per_sm(const void *kernel, int threads, size_t smem) {
     return blocks;
 }
 
+// Looks up cuTensorMapEncodeTiled once; false if the driver lacks it.
+static bool encode_lines_map_ready() {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_encode_tried) {
+        g_encode_tried = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    }
+    return g_encode != nullptr;
+}
+
 bool encode_lines_map(void *map, const void *base, int esz, int64_t inner, int64_t n,
                       int64_t outer, int box_x, int box_rows) {
-    {
-        std::lock_guard<std::mutex> lk(g_pool_mu);
-        if (!g_encode_tried) {
-            g_encode_tried = true;
-            void *fn = nullptr;
-            cudaDriverEntryPointQueryResult q;
-            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                 cudaEnableDefault, &q) == cudaSuccess &&
-                q == cudaDriverEntryPointSuccess)
-                g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-            else
-                cudaGetLastError();
-        }
-    }
-    if (!g_encode) return false;
+    if (!encode_lines_map_ready()) return false;
     if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
     const int64_t rows = box_rows > 0 ? box_rows : n;
     if ((inner * esz) % 16 != 0 || n < 1 || rows > 256 || inner < 1 || outer < 1) return false;
@@ -177,6 +180,31 @@ bool encode_lines_map(void *map, const void *base, int esz, int64_t inner, int64
         const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool encode_rows_map(void *map, const void *base, int esz, int64_t row_elems, int64_t nrows,
+                     int box_rows, int swizzle) {
+    if (!encode_lines_map_ready()) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+    const int64_t row_bytes = row_elems * esz;
+    if (row_bytes % 16 != 0 || row_bytes > swizzle || nrows < 1 || box_rows < 1 ||
+        box_rows > 256 || nrows >= (int64_t(1) << 32))
+        return false;
+    CUtensorMapSwizzle sw;
+    if (swizzle == 32) sw = CU_TENSOR_MAP_SWIZZLE_32B;
+    else if (swizzle == 64) sw = CU_TENSOR_MAP_SWIZZLE_64B;
+    else if (swizzle == 128) sw = CU_TENSOR_MAP_SWIZZLE_128B;
+    else return false;
+    const cuuint64_t dims[2] = {cuuint64_t(row_elems), cuuint64_t(nrows)};
+    const cuuint64_t strides[1] = {cuuint64_t(row_bytes)};
+    const cuuint32_t box[2] = {cuuint32_t(row_elems), cuuint32_t(box_rows)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = g_encode(
+        static_cast<CUtensorMap *>(map),
+        esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+        const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 

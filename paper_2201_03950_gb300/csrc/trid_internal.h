@@ -31,6 +31,13 @@ const DeviceInfo *device_info();
 bool encode_lines_map(void *map /* CUtensorMap */, const void *base, int esz, int64_t inner,
                       int64_t n, int64_t outer, int box_x, int box_rows = 0);
 
+// 2D tensor map over `nrows` rows of `row_elems` contiguous elements (row
+// pitch = row_elems), box (row_elems, box_rows), shared-memory swizzle of
+// 32, 64 or 128 bytes (row_elems * esz <= swizzle); false if the TMA
+// constraints do not hold.
+bool encode_rows_map(void *map /* CUtensorMap */, const void *base, int esz, int64_t row_elems,
+                     int64_t nrows, int box_rows, int swizzle);
+
 // Clusters of `csize` CTAs of `kernel` that can be resident at once (0 if
 // none or the query fails); sizes above 8 are enabled on the function first.
 int cluster_capacity(const void *kernel, int csize, int threads, size_t smem);

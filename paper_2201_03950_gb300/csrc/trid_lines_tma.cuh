@@ -100,14 +100,17 @@ struct LinesTmaLayout {
     static constexpr int TT = 32 * TW;               // threads per team
     static constexpr int NTEAM = LT_CONS / TT;       // teams per block
     static_assert(NTEAM % SPS == 0, "teams split evenly over the systems of a stage");
+    // slots on 1024-byte boundaries (the swizzled boxes' pattern repeats every 512 bytes)
     __host__ __device__ static size_t slot_bytes(int n) {
-        return (size_t(SPS) * n * sizeof(T) + 127) / 128 * 128;
+        return (size_t(SPS) * n * sizeof(T) + 1023) / 1024 * 1024;
     }
     __host__ __device__ static size_t red_bytes() {
         return 2 * size_t(NTEAM) * 3 * 2 * TT * sizeof(T);
     }
+    // + 1 KB so that the stages can start on a 1024-byte boundary (swizzled copies)
     __host__ __device__ static size_t bytes(int n, int narr, int stages) {
-        return size_t(stages) * narr * slot_bytes(n) + red_bytes() + 2 * stages * sizeof(uint64_t);
+        return size_t(stages) * narr * slot_bytes(n) + red_bytes() + 2 * stages * sizeof(uint64_t) +
+               1024;
     }
 };
 
@@ -116,16 +119,27 @@ struct LinesTmaLayout {
 // systems, and the NTEAM / SPS groups of SPS teams take the stages in turn.
 // Requirements (host): every pointer 16-byte aligned, n % 4 == 0 (FP32),
 // n <= M * 32 * TW.
-template <typename T, int TW, int M, int SPS>
+// SWZ (rows of M * sizeof(T) = 32 or 64 bytes, n % M == 0, every system's
+// region 1024-byte aligned): each array of a system arrives as one 2D TMA
+// box of n / M rows with the 32- or 64-byte shared-memory swizzle (maps: a,
+// c, d, b), which puts the 16-byte chunk q of a row at chunk q ^ (address
+// bits 7.. of the row) -- bit 7 for 32-byte rows, bits 7-8 for 64-byte rows;
+// a warp reading chunk q of 32 consecutive rows then touches 32 different
+// banks (the plain layout gives a 2- or 4-way conflict at that lane stride).
+template <typename T, int TW, int M, int SPS, bool SWZ>
 __global__ void __launch_bounds__(LT_CONS + 32, 1)
-k_lines_tma(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c,
-            const T *d, T *out, int accumulate, int nsys, int n, int nbatch, int stages,
-            int *status) {
+k_lines_tma(const __grid_constant__ TmaSet maps, const T *__restrict__ a,
+            const T *__restrict__ b, const T *__restrict__ c, const T *d, T *out,
+            int accumulate, int nsys, int n, int nbatch, int stages, int *status) {
+    static_assert(!SWZ || M * sizeof(T) == 32 || M * sizeof(T) == 64,
+                  "swizzled rows are 32 or 64 bytes");
     using LY = LinesTmaLayout<T, TW, SPS>;
     constexpr int TT = LY::TT;
     constexpr int NTEAM = LY::NTEAM;
     constexpr int NG = NTEAM / SPS;  // team groups, taking stages in turn
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // stages on a 1024-byte boundary (the swizzle pattern follows address bits)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int narr = b ? 4 : 3;
     const size_t slot = LY::slot_bytes(n);
     const size_t stage_bytes = size_t(narr) * slot;
@@ -162,9 +176,18 @@ k_lines_tma(const T *__restrict__ a, const T *__restrict__ b, const T *__restric
                 const uint32_t bytes = uint32_t(cnt) * uint32_t(n) * uint32_t(sizeof(T));
                 mbar_expect_tx(&full[s], uint32_t(narr) * bytes);
                 unsigned char *dst = smem + s * stage_bytes;
-                const size_t off = size_t(sys0) * size_t(n);
-                for (int q = 0; q < narr; ++q)
-                    bulk_load_1d(dst + q * slot, src[q] + off, bytes, &full[s]);
+                if (SWZ) {
+                    const int rows = n / M;
+                    const size_t sb = size_t(n) * sizeof(T);
+                    for (int q = 0; q < narr; ++q)
+                        for (int j = 0; j < cnt; ++j)
+                            tma_load_2d(dst + q * slot + j * sb, &maps.map[q], 0,
+                                        (sys0 + j) * rows, &full[s]);
+                } else {
+                    const size_t off = size_t(sys0) * size_t(n);
+                    for (int q = 0; q < narr; ++q)
+                        bulk_load_1d(dst + q * slot, src[q] + off, bytes, &full[s]);
+                }
             }
         }
         return;
@@ -196,7 +219,49 @@ k_lines_tma(const T *__restrict__ a, const T *__restrict__ b, const T *__restric
         const T *sd = reinterpret_cast<const T *>(stg + 2 * slot) + row0;
         const T *sb = reinterpret_cast<const T *>(stg + 3 * slot) + row0;
         T ra[M], rb[M], rc[M], rd[M];
-        if (active && mine && full_tile) {
+        if (SWZ) {
+            // row t of the box: chunk q at chunk q ^ x of the row (x from the
+            // row's shared-memory address bits 7-8)
+            using V = typename Vec16<T>::type;
+            constexpr int W = Vec16<T>::n;
+            const size_t r = row0 / W;  // 16-byte chunk of the row's start
+            const V *va = reinterpret_cast<const V *>(stg) + r;
+            const V *vc = reinterpret_cast<const V *>(stg + slot) + r;
+            const V *vd = reinterpret_cast<const V *>(stg + 2 * slot) + r;
+            const V *vb = reinterpret_cast<const V *>(stg + 3 * slot) + r;
+            const int x = int((smem_u32(va) >> 7) & unsigned(M / W - 1));
+#pragma unroll
+            for (int q = 0; q < M / W; ++q) {
+                const int pq = q ^ x;
+                V w;
+                if (active && mine) {
+                    w = va[pq];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) ra[q * W + j] = reinterpret_cast<const T *>(&w)[j];
+                    w = vc[pq];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) rc[q * W + j] = reinterpret_cast<const T *>(&w)[j];
+                    w = vd[pq];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) rd[q * W + j] = reinterpret_cast<const T *>(&w)[j];
+                    if (b) {
+                        w = vb[pq];
+#pragma unroll
+                        for (int j = 0; j < W; ++j)
+                            rb[q * W + j] = reinterpret_cast<const T *>(&w)[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < W; ++j) rb[q * W + j] = T(1);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        ra[q * W + j] = T(0); rb[q * W + j] = T(1);
+                        rc[q * W + j] = T(0); rd[q * W + j] = T(0);
+                    }
+                }
+            }
+        } else if (active && mine && full_tile) {
             load_contig_vec<T, M>(sa, ra);
             load_contig_vec<T, M>(sc, rc);
             load_contig_vec<T, M>(sd, rd);

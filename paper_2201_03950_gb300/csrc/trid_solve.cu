@@ -296,7 +296,7 @@ static void launch_strided(const T *a, const T *b, const T *c, const T *d, T *ou
 // Contiguous FP32 systems of 256 < n <= 4096 through k_lines_tma with teams
 // of TW warps, M rows per thread (n <= 32 * TW * M).  False, having launched nothing, when the
 // shared memory does not fit.
-template <int TW, int M, int SPS>
+template <int TW, int M, int SPS, bool SWZ = false>
 static bool launch_lines_tma_tw(const float *a, const float *b, const float *c, const float *d,
                                 float *out, int acc, const Lines &L, cudaStream_t st) {
     using LY = LinesTmaLayout<float, TW, SPS>;
@@ -308,14 +308,26 @@ static bool launch_lines_tma_tw(const float *a, const float *b, const float *c, 
     while (stages > 2 && LY::bytes(n, narr, stages) > size_t(di->max_smem_optin)) --stages;
     const size_t smem = LY::bytes(n, narr, stages);
     if (smem > size_t(di->max_smem_optin)) return false;
-    auto kern = k_lines_tma<float, TW, M, SPS>;
+    TmaSet maps{};  // used by the swizzled variant only
+    if constexpr (SWZ) {
+        // one 2D box of n / M rows of M elements per array and system, swizzled
+        // by the row size; several systems per stage need 1024-byte regions
+        if (n % M != 0 || (SPS > 1 && n % 256 != 0) ||
+            L.nsys * (L.n / M) >= (int64_t(1) << 31))
+            return false;
+        const float *arr[4] = {a, c, d, b};
+        for (int q = 0; q < narr; ++q)
+            if (!encode_rows_map(&maps.map[q], arr[q], 4, M, L.nsys * (L.n / M), n / M, M * 4))
+                return false;
+    }
+    auto kern = k_lines_tma<float, TW, M, SPS, SWZ>;
     const int per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), LT_CONS + 32, smem);
     if (per_sm < 1) return false;
     const int64_t nbatch = (L.nsys + SPS - 1) / SPS;
     const int64_t slots = int64_t(di->sm_count) * per_sm;
     const int64_t grid = nbatch < slots ? nbatch : slots;
-    kern<<<dim3(unsigned(grid)), LT_CONS + 32, smem, st>>>(a, b, c, d, out, acc, int(L.nsys), n,
-                                                           int(nbatch), stages,
+    kern<<<dim3(unsigned(grid)), LT_CONS + 32, smem, st>>>(maps, a, b, c, d, out, acc,
+                                                           int(L.nsys), n, int(nbatch), stages,
                                                            device_status_word());
     return cudaGetLastError() == cudaSuccess;
 }
@@ -331,12 +343,17 @@ static bool launch_lines_tma(const T *a, const T *b, const T *c, const T *d, T *
         if (L.stride != 1 || !aligned || L.n % 4 != 0 || L.n <= MAX_SINGLE_PASS ||
             L.n > LT_MAX_N || L.nsys >= (int64_t(1) << 31) || L.nsys * L.n >= (int64_t(1) << 40))
             return false;
+        // 8 rows per thread: one contiguous bulk copy per array and stage
+        // (per-system swizzled 32-byte-row boxes measured slower at 1024 and
+        // 2048 rows)
         if (L.n <= 512) return launch_lines_tma_tw<2, 8, 8>(a, b, c, d, out, acc, L, st);
         if (L.n <= 1024) return launch_lines_tma_tw<4, 8, 4>(a, b, c, d, out, acc, L, st);
         if (L.n <= 2048) return launch_lines_tma_tw<8, 8, 2>(a, b, c, d, out, acc, L, st);
         // two teams of 8 warps, 16 rows per thread, taking one-system stages
-        // in turn: two systems in flight
-        return launch_lines_tma_tw<8, 16, 1>(a, b, c, d, out, acc, L, st);
+        // in turn: two systems in flight; swizzled 64-byte-row boxes when
+        // n % 16 == 0
+        return launch_lines_tma_tw<8, 16, 1, true>(a, b, c, d, out, acc, L, st) ||
+               launch_lines_tma_tw<8, 16, 1>(a, b, c, d, out, acc, L, st);
     }
 }
 
