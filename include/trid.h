@@ -79,13 +79,18 @@ const char *trid_last_cuda_error(void);
  *                    "u = u + d").  u must not alias a, b, c or d.
  *   dtype            TRID_F32 or TRID_F64; all arrays share it.
  *
- * Systems longer than the on-chip limit of the single-pass kernels (256 in
- * this build) are solved with the tiled Thomas-PCR hybrid of Section 3.1 in
- * several passes; those passes need scratch of
- * trid_solve_workspace_bytes(...) bytes, which this entry point takes from a
- * library-owned pool (grown with cudaMalloc on first need; that first call
- * must not be inside a stream capture).  Use trid_solve_batch_ws to pass
- * caller-owned scratch instead.
+ * Systems of up to 256 rows are solved in one pass with the tiled hybrid of
+ * Section 3.1 held in registers.  Longer FP32 systems of up to 4096 rows
+ * are solved in one pass too, without scratch, when their arrays start on
+ * 16-byte boundaries and (contiguous systems) the length is a multiple of 4
+ * or (strided systems) the contiguous extent times 4 bytes is a multiple of
+ * 16: whole systems staged in shared memory, or one thread-block cluster per
+ * strip of 16 systems.  All other long systems (longer, FP64, unaligned) go
+ * through the hybrid in several passes, which need scratch of
+ * trid_solve_workspace_bytes(...) bytes; this entry point takes it from a
+ * library-owned pool, grown with cudaMalloc only when the multi-pass path is
+ * taken (that first call must not be inside a stream capture).  Use
+ * trid_solve_batch_ws to pass caller-owned scratch instead.
  * No numerical pivoting: the caller guarantees a nonsingular system for
  * which Gaussian elimination without pivoting is stable (e.g. diagonally
  * dominant rows).  An exact zero pivot yields inf/nan, not an error code.
@@ -94,8 +99,10 @@ trid_status trid_solve_batch(const void *a, const void *b, const void *c, void *
                              const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
                              trid_stream_t stream);
 
-/* Scratch bytes trid_solve_batch_ws needs for this problem (0 when the
- * single-pass kernels serve it).  Returns 0 as well for invalid arguments. */
+/* Scratch bytes trid_solve_batch_ws needs for this problem: 0 for systems of
+ * up to 256 rows, else what the multi-pass path needs (an upper bound: the
+ * one-pass long-system kernels need none, but whether they apply depends on
+ * the arrays' alignment).  Returns 0 as well for invalid arguments. */
 size_t trid_solve_workspace_bytes(const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype);
 
 /* As trid_solve_batch, with caller-owned device scratch `workspace` of
@@ -173,11 +180,11 @@ size_t trid_solve_varlen_workspace_bytes(int64_t nsys);
  * latency-critical loop that must not pay the device-wide synchronisation of
  * growing trid_solve_batch's scratch pool.
  *
- * Same arguments and results as trid_solve_batch.  Systems longer than 256
- * need scratch (trid_solve_workspace_bytes); here it comes from one fixed
- * device array of TRID_NOALLOC_SCRATCH_BYTES (32 MiB) that the library holds
- * on every GPU that loads it, until the process exits.  The call never
- * allocates or frees device memory.
+ * Same arguments and results as trid_solve_batch.  Long systems that the
+ * one-pass kernels do not take need scratch (trid_solve_workspace_bytes);
+ * here it comes from one fixed device array of TRID_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) that the library holds on every GPU that loads it, until the
+ * process exits.  The call never allocates or frees device memory.
  *   - Problems needing more scratch than TRID_NOALLOC_SCRATCH_BYTES are
  *     rejected with TRID_ERR_ALLOC before anything is launched (use
  *     trid_solve_batch_ws with your own buffer for those).

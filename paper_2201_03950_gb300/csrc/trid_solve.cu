@@ -566,8 +566,10 @@ static trid_status solve_dispatch(const void *a, const void *b, const void *c, v
 
 // Argument check, scratch size and dispatch for a caller that supplies its own
 // scratch (used by the allocation-free entry point).  `need` receives the
-// scratch bytes the problem requires; nothing is launched when the returned
-// status is not TRID_OK or when `scratch_bytes < need`.
+// scratch bytes the multi-pass path would require.  With less scratch than
+// that the problem is still solved when the one-pass long-system kernels take
+// it (they need none); otherwise TRID_ERR_ALLOC is returned and nothing is
+// launched.
 trid_status solve_with_scratch(const void *a, const void *b, const void *c, void *d, void *u,
                                const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
                                void *scratch, size_t scratch_bytes, size_t &need,
@@ -588,7 +590,8 @@ trid_status solve_with_scratch(const void *a, const void *b, const void *c, void
     trid_status s = check_solve_args(a, b, c, d, u, dims, ndim, solve_dim, dtype, L, esz);
     if (s != TRID_OK || L.nsys == 0 || L.n == 0) return s;
     need = solve_ws_bytes(L, dtype);
-    if (need > scratch_bytes) return TRID_ERR_ALLOC;
+    if (need > scratch_bytes)  // OK if a one-pass kernel took it, else ALLOC with nothing launched
+        return solve_dispatch(a, b, c, d, u, L, dtype, nullptr, 0, st);
     return solve_dispatch(a, b, c, d, u, L, dtype, static_cast<char *>(scratch), scratch_bytes, st);
 }
 
@@ -628,11 +631,15 @@ extern "C" trid_status trid_solve_batch(const void *a, const void *b, const void
     trid_status s = check_solve_args(a, b, c, d, u, dims, ndim, solve_dim, dtype, L, esz);
     if (s != TRID_OK || L.nsys == 0 || L.n == 0) return s;
     const size_t need = solve_ws_bytes(L, dtype);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     void *ws = nullptr;
     if (need > 0) {
+        // the one-pass long-system kernels need no scratch: only when they
+        // decline (nothing launched, TRID_ERR_ALLOC) is the pool grown
+        s = solve_dispatch(a, b, c, d, u, L, dtype, nullptr, 0, st);
+        if (s != TRID_ERR_ALLOC) return s;
         s = pool_reserve(need, &ws);
         if (s != TRID_OK) return s;
     }
-    return solve_dispatch(a, b, c, d, u, L, dtype, static_cast<char *>(ws), need,
-                          reinterpret_cast<cudaStream_t>(stream));
+    return solve_dispatch(a, b, c, d, u, L, dtype, static_cast<char *>(ws), need, st);
 }

@@ -82,3 +82,21 @@ def test_noalloc_short_systems_need_no_scratch(lib):
     trid.solve_noalloc(ta, tb, tc, td, dims, 0)
     torch.cuda.synchronize()
     assert normwise(td.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [0, 1], ids=["x", "y"])
+def test_noalloc_one_pass_long_systems_need_no_scratch(lib, k):
+    """4096 x 4096 FP32: the multi-pass scratch of this problem exceeds the
+    fixed array, but the one-pass long-system kernels take it without
+    scratch, so the allocation-free call solves it (the same kernels as
+    trid_solve_batch: identical bits)."""
+    dims = (4096, 4096)
+    need = lib.trid_solve_workspace_bytes((ctypes.c_int64 * 2)(*dims), 2, k, 0)
+    assert need > lib_max()
+    a, b, c, d = inputs.dominant_system((4096 * 4096,), seed=31 + k, dtype=np.float32)
+    ta, tb, tc, td = (torch.from_numpy(v).cuda() for v in (a, b, c, d))
+    td_ref = td.clone()
+    assert _call(lib, lib.trid_solve_batch, ta, tb, tc, td_ref, dims, k, 0) == 0
+    assert _call(lib, lib.trid_solve_batch_noalloc, ta, tb, tc, td, dims, k, 0) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(td, td_ref)
