@@ -74,7 +74,7 @@ const char *trid_last_cuda_error(void);
  *   a, b, c          coefficients; a at the first element and c at the last
  *                    element of every system are NOT read (treated as 0).
  *   d                right-hand side.
- *   u == NULL        x overwrites d in place (the listing's "update d").
+ *   u == NULL        x overwrites d in place (Algorithm "thomas" updates d).
  *   u != NULL        u += x and d is left unmodified (Algorithm "adi",
  *                    "u = u + d").  u must not alias a, b, c or d.
  *   dtype            TRID_F32 or TRID_F64; all arrays share it.

@@ -35,7 +35,7 @@
 /*             r = 1/(b_i - a_i c*_{i-1}); d*_i = r (d_i - a_i d*_{i-1});     */
 /*             c*_i = r c_i                      for i = 1..N-1               */
 /*   backward: x_{N-1} = d*_{N-1};  x_i = d*_i - c*_i x_{i+1}, i = N-2..0      */
-/* The listing leaves x_{N-1} = d*_{N-1} implicit (it overwrites d in place); */
+/* Algorithm "thomas" leaves x_{N-1} = d*_{N-1} implicit (it overwrites d);   */
 /* it is written out here.                                                    */
 /* ------------------------------------------------------------------------ */
 int orc_thomas(int64_t n, const double *a, const double *b, const double *c,
@@ -323,9 +323,9 @@ out:
 /*      operator tridiag(-lambda, 1 + 2 lambda, -lambda) on interior rows and */
 /*      identity rows (a = c = 0, b = 1) at the two Dirichlet boundary nodes; */
 /*   3. u = u + d.                                                            */
-/* Readings: the listing's garbled coefficients (a = c = -gamma/2, b = gamma) */
-/* are read as a = c = -lambda, b = 1 + 2 lambda; the boundary is Dirichlet   */
-/* zero (boundary nodes never change).  ndim is 2 or 3.                       */
+/* Readings: Algorithm "adi" prints garbled coefficients (a = c = -gamma/2,  */
+/* b = gamma); they are read as a = c = -lambda, b = 1 + 2 lambda.  The       */
+/* boundary is Dirichlet zero (boundary nodes never change).  ndim is 2 or 3. */
 /* ------------------------------------------------------------------------ */
 int orc_adi(double *u, const int64_t *dims, int ndim, double lambda, int nsteps)
 {
