@@ -58,6 +58,18 @@ def parse():
     return p.parse_args()
 
 
+def aggregate_ranks(ms_step, step_bytes, world, dist=None, device="cpu"):
+    """Whole-job figure of `world` independent replicas (weak scaling): the
+    slowest rank's time per step (max over ranks) and every rank's bytes.
+    Returns (ms per step, GB/s)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(ms_step)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    return ms_step, world * step_bytes / (ms_step * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -246,12 +258,8 @@ def run_ours(args):
         for n, e0, e1 in evs:
             per[n].append(e0.elapsed_time(e1))
     ms_step = sum(sum(v) for v in per.values()) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
     step_bytes = sum(nbytes.values())
-    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    ms_step, value = aggregate_ranks(ms_step, step_bytes, world, dist if world > 1 else None, dev)
 
     # ---- secondary workload: 4096^2 FP32, few long systems (tiled Thomas-PCR
     #      passes), along x and y; same restore + flush protocol, mean of 5
@@ -556,8 +564,10 @@ def run_ours(args):
     if args.e2e_steps > 0:
         e2e_run(2)  # warm-up
         e2e_ms = [e2e_run(args.e2e_steps)]
-    e2e_step_ms = statistics.median(e2e_ms) if e2e_ms else None
-    e2e_val = world * step_bytes / (e2e_step_ms * 1e-3) / 1e9 if e2e_ms else None
+    e2e_step_ms, e2e_val = None, None
+    if e2e_ms:
+        e2e_step_ms, e2e_val = aggregate_ranks(statistics.median(e2e_ms), step_bytes, world,
+                                               dist if world > 1 else None, dev)
 
     peak, peak_kind = peaks()
     means = {n: statistics.mean(v) for n, v in per.items()}
