@@ -3,16 +3,19 @@
 // neighbouring systems (arXiv 2201.03950, Section 3.1: the tiled hybrid
 // applied once more, one level up).
 //
-// A system is cut into C = ceil(N / 256) chunks of 256 rows; CTA `rank` of a
+// A system is cut into C <= 8 chunks of CH rows (CH = 256 for N <= 2048, with
+// 8 rows per thread and two CTAs per SM; CH = 512 above, with 16 rows per
+// thread and one CTA per SM, which halves the per-chunk barriers and
+// exchanges per byte); CTA `rank` of a
 // cluster of C CTAs owns chunk `rank` of the strip.  By linearity the
 // solution restricted to a chunk is
 //     x = p + q * x_L + r * x_R
 // where x_L, x_R are the unknowns just outside the chunk, p solves the chunk
 // with x_L = x_R = 0 and q, r are its responses to x_L = 1 and x_R = 1.
 //
-//  1. TMA loads the chunk's [16 systems x 256 rows] box of a, b, c, d; each
-//     of the 512 threads takes one tile of 8 rows of one system into
-//     registers, and the next strip's box is requested at once.
+//  1. TMA loads the chunk's [16 systems x CH rows] of a, b, c, d (boxes of
+//     256 rows); each of the 512 threads takes one tile (CH / 32 rows) of one
+//     system into registers, and the next strip's boxes are requested at once.
 //  2. tile_reduce, then one warp per system solves the chunk's reduced
 //     system (PCR over 32 tiles, as group_solve) for p, q and r at once:
 //     every tile end's p, q, r value stays in the solving lane's registers.
@@ -36,17 +39,19 @@ namespace trid {
 
 constexpr int CK_NT = 32;            // tiles per chunk (one warp per system)
 constexpr int CK_SG = 16;            // neighbouring systems per strip
-constexpr int CK_ROWS = CK_NT * 8;   // rows per chunk
+constexpr int CK_BOX = 256;          // rows per TMA box
 constexpr int CK_THREADS = CK_NT * CK_SG;
-constexpr int CK_MAX_CHUNKS = 16;    // cluster size limit (non-portable 16)
+constexpr int CK_MAX_CHUNKS = 8;     // cluster size (portable)
 
 // Shared memory: the chunk's box of 4 arrays, the reduced tables (6 rows + 2
 // solutions per tile, row pitch SG + 1), two buffers of F/E values (6 x SG),
 // the gathered values of all chunks (C x 6 x SG) and the mbarrier.
-template <typename T>
+// CM rows per thread: chunks of CK_NT * CM rows (256 or 512).
+template <typename T, int CM>
 struct ChunkLayout {
     static constexpr int P = CK_SG + 1;
-    __host__ __device__ static size_t slot_bytes() { return size_t(CK_ROWS) * CK_SG * sizeof(T); }
+    static constexpr int ROWS = CK_NT * CM;
+    __host__ __device__ static size_t slot_bytes() { return size_t(ROWS) * CK_SG * sizeof(T); }
     __host__ __device__ static size_t tab_off() { return 4 * slot_bytes(); }
     __host__ __device__ static size_t spk_off() { return tab_off() + 8 * CK_NT * P * sizeof(T); }
     __host__ __device__ static size_t gat_off() { return spk_off() + 2 * 6 * CK_SG * sizeof(T); }
@@ -112,13 +117,14 @@ __device__ __forceinline__ void group_solve_spikes(T as, T cs, T ds, T ae, T ce,
 
 // Strip s -> (outer o, x-group xg); the cluster walks strips with stride
 // nclusters.  TMA map over (inner, n, outer), box (SG, 256, 1).
-template <typename T>
-__global__ void __launch_bounds__(CK_THREADS, 2)
+template <typename T, int CM>
+__global__ void __launch_bounds__(CK_THREADS, CM == 8 ? 2 : 1)
 k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lines L,
                 int nstrips, int *status) {
     namespace cg = cooperative_groups;
-    constexpr int NT = CK_NT, SG = CK_SG, M = 8, CH = CK_ROWS;
-    using LY = ChunkLayout<T>;
+    constexpr int NT = CK_NT, SG = CK_SG, M = CM, CH = CK_NT * CM;
+    static_assert(CH % CK_BOX == 0, "a chunk is whole TMA boxes");
+    using LY = ChunkLayout<T, CM>;
     constexpr int P = LY::P;
     extern __shared__ __align__(128) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -157,7 +163,10 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
         mbar_expect_tx(full, tx);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            tma_load_3d(smem + q * LY::slot_bytes(), &maps.map[q], xg * SG, rank * CH, o, full);
+#pragma unroll
+            for (int h = 0; h < CH / CK_BOX; ++h)
+                tma_load_3d(smem + q * LY::slot_bytes() + size_t(h) * CK_BOX * SG * sizeof(T),
+                            &maps.map[q], xg * SG, rank * CH + h * CK_BOX, o, full);
     };
     if (tid == 0 && cid < nstrips) issue(cid);
 

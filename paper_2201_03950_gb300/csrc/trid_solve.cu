@@ -24,8 +24,8 @@
 //             whole systems staged in shared memory by bulk copies, one team
 //             of warps per system (trid_lines_tma.cuh).
 //  k_chunk_cluster  strided FP32 systems of 256 < N <= 4096 in one pass:
-//             chunks of 256 rows, one CTA each, joined by a chunk-level solve
-//             across a thread-block cluster (trid_chunked.cuh).
+//             chunks of 256 or 512 rows, one CTA each, joined by a chunk-level
+//             solve across a thread-block cluster (trid_chunked.cuh).
 #include "trid_device.cuh"
 #include "trid_strided.cuh"
 #include "trid_lines_tma.cuh"
@@ -358,56 +358,68 @@ static bool launch_lines_tma(const T *a, const T *b, const T *c, const T *d, T *
 }
 
 // Strided FP32 systems of 256 < n <= 4096 rows through k_chunk_cluster: one
-// cluster of C = ceil(n / 256) CTAs per strip of 16 systems, as many clusters
-// as can be resident.  False, having launched nothing, when a constraint
-// (TMA alignment, 32-bit indexing, cluster scheduling) does not hold.
+// cluster of C = ceil(n / (32 CM)) CTAs per strip of 16 systems, as many
+// clusters as can be resident.  CM = 8 rows per thread (256-row chunks, two
+// CTAs per SM) up to 2048 rows, CM = 16 (512-row chunks, one CTA per SM:
+// half the per-chunk barriers and exchanges per byte) above.  False, having
+// launched nothing, when a constraint (TMA alignment, 32-bit indexing,
+// cluster scheduling) does not hold.
+template <typename T, int CM>
+static bool launch_chunk_cluster_cm(const T *a, const T *b, const T *c, const T *d, T *out,
+                                    int acc, const Lines &L, cudaStream_t st) {
+    using LY = ChunkLayout<T, CM>;
+    const int C = int((L.n + LY::ROWS - 1) / LY::ROWS);
+    if (C > CK_MAX_CHUNKS) return false;
+    const int64_t outer = L.nsys / L.inner;
+    const int64_t nxc = (L.inner + CK_SG - 1) / CK_SG;
+    const int64_t nstrips = nxc * outer;
+    if (nstrips >= (int64_t(1) << 31) || L.inner >= (int64_t(1) << 31)) return false;
+    TmaSet maps;
+    const void *arrs[4] = {a, b, c, d};
+    for (int q = 0; q < 4; ++q)
+        if (!encode_lines_map(&maps.map[q], arrs[q], int(sizeof(T)), L.inner, L.n, outer, CK_SG,
+                              CK_BOX))
+            return false;
+    const size_t smem = LY::bytes(C);
+    auto kern = k_chunk_cluster<T, CM>;
+    const void *kp = reinterpret_cast<const void *>(kern);
+    if (kernel_blocks_per_sm(kp, CK_THREADS, smem) < 1) return false;
+    const int ncl_max = cluster_capacity(kp, C, CK_THREADS, smem);
+    if (ncl_max < 1) return false;
+    const int64_t ncl = nstrips < ncl_max ? nstrips : ncl_max;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(C);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(unsigned(C * ncl));
+    cfg.blockDim = dim3(CK_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, out, acc, L, int(nstrips),
+                                             device_status_word());
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 template <typename T>
 static bool launch_chunk_cluster(const T *a, const T *b, const T *c, const T *d, T *out, int acc,
                                  const Lines &L, cudaStream_t st) {
     if constexpr (!std::is_same<T, float>::value) {
         return false;
     } else {
-        if (L.stride == 1 || !b || L.n <= MAX_SINGLE_PASS ||
-            L.n > int64_t(CK_ROWS) * CK_MAX_CHUNKS || !strided_offsets_fit(L))
+        if (L.stride == 1 || !b || L.n <= MAX_SINGLE_PASS || L.n > 4096 ||
+            !strided_offsets_fit(L))
             return false;
-        const int C = int((L.n + CK_ROWS - 1) / CK_ROWS);
-        const int64_t outer = L.nsys / L.inner;
-        const int64_t nxc = (L.inner + CK_SG - 1) / CK_SG;
-        const int64_t nstrips = nxc * outer;
-        if (nstrips >= (int64_t(1) << 31) || L.inner >= (int64_t(1) << 31)) return false;
-        TmaSet maps;
-        const void *arrs[4] = {a, b, c, d};
-        for (int q = 0; q < 4; ++q)
-            if (!encode_lines_map(&maps.map[q], arrs[q], int(sizeof(T)), L.inner, L.n, outer,
-                                  CK_SG, CK_ROWS))
-                return false;
-        const size_t smem = ChunkLayout<T>::bytes(C);
-        auto kern = k_chunk_cluster<T>;
-        const void *kp = reinterpret_cast<const void *>(kern);
-        if (kernel_blocks_per_sm(kp, CK_THREADS, smem) < 1) return false;
-        const int ncl_max = cluster_capacity(kp, C, CK_THREADS, smem);
-        if (ncl_max < 1) return false;
-        const int64_t ncl = nstrips < ncl_max ? nstrips : ncl_max;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = unsigned(C);
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(unsigned(C * ncl));
-        cfg.blockDim = dim3(CK_THREADS);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, out, acc, L, int(nstrips),
-                                                 device_status_word());
-        if (e != cudaSuccess) {
-            note_cuda_error(e);
-            cudaGetLastError();
-            return false;
-        }
-        return true;
+        if (L.n <= 2048) return launch_chunk_cluster_cm<T, 8>(a, b, c, d, out, acc, L, st);
+        return launch_chunk_cluster_cm<T, 16>(a, b, c, d, out, acc, L, st);
     }
 }
 
