@@ -59,7 +59,9 @@ struct ChunkLayout {
         return (gat_off() + size_t(C) * 6 * CK_SG * sizeof(T) + 2 * 2 * CK_SG * sizeof(T) + 15) /
                16 * 16;
     }
-    __host__ __device__ static size_t bytes(int C) { return bar_off(C) + 16; }
+    // x staging for the TMA store of the chunk (same [row][SG] layout)
+    __host__ __device__ static size_t xst_off(int C) { return (bar_off(C) + 16 + 127) / 128 * 128; }
+    __host__ __device__ static size_t bytes(int C) { return xst_off(C) + slot_bytes(); }
 };
 
 // group_solve (full warp, G = 32 tiles) for three right-hand sides that
@@ -120,7 +122,7 @@ __device__ __forceinline__ void group_solve_spikes(T as, T cs, T ds, T ae, T ce,
 template <typename T, int CM>
 __global__ void __launch_bounds__(CK_THREADS, CM == 8 ? 2 : 1)
 k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lines L,
-                int nstrips, int *status) {
+                int nstrips, int tma_store, int *status) {
     namespace cg = cooperative_groups;
     constexpr int NT = CK_NT, SG = CK_SG, M = CM, CH = CK_NT * CM;
     static_assert(CH % CK_BOX == 0, "a chunk is whole TMA boxes");
@@ -144,6 +146,7 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
     T *gat = reinterpret_cast<T *>(smem + LY::gat_off());     // [C][6][SG]
     T *xlr = gat + size_t(C) * 6 * SG;                        // [2][SG]: x_L, x_R
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + LY::bar_off(C));
+    T *xst = reinterpret_cast<T *>(smem + LY::xst_off(C));
 
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
@@ -261,7 +264,28 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
         }
         __syncthreads();
         tile_substitute<T, M>(ra, rc, rd, s_xs[w], s_xe[w]);
-        if (active) {
+        if (tma_store) {
+            // x leaves through the shared-memory box and one TMA store per
+            // 256 rows: the async stores stay out of every thread's release
+            // fence at the next cluster barrier (global stores issued by the
+            // threads would have to complete there first)
+            if (tid == 0) bulk_wait_read_all();  // the previous strip's store has read xst
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < M; ++k) xst[(i0 + k) * SG + sl] = rd[k];
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0 && ok) {
+#pragma unroll
+                for (int h = 0; h < CH / CK_BOX; ++h)
+                    if (g0 + h * CK_BOX < n)  // rows past n (and x past inner) are clipped
+                        tma_store_3d(&maps.map[4], xg * SG, g0 + h * CK_BOX, o,
+                                     xst + size_t(h) * CK_BOX * SG);
+                bulk_commit();
+            }
+        } else if (active) {
             T *ob = out + (int64_t(o) * L.inner * L.n + x);
 #pragma unroll
             for (int k = 0; k < M; ++k) {
@@ -273,6 +297,7 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
             }
         }
     }
+    if (tma_store && tid == 0) bulk_wait_all();  // every store of this CTA has landed
     cluster.sync();  // no CTA leaves while a peer may still read its values
 }
 

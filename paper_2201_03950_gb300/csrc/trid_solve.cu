@@ -374,12 +374,16 @@ static bool launch_chunk_cluster_cm(const T *a, const T *b, const T *c, const T 
     const int64_t nxc = (L.inner + CK_SG - 1) / CK_SG;
     const int64_t nstrips = nxc * outer;
     if (nstrips >= (int64_t(1) << 31) || L.inner >= (int64_t(1) << 31)) return false;
-    TmaSet maps;
+    TmaSet maps{};
     const void *arrs[4] = {a, b, c, d};
     for (int q = 0; q < 4; ++q)
         if (!encode_lines_map(&maps.map[q], arrs[q], int(sizeof(T)), L.inner, L.n, outer, CK_SG,
                               CK_BOX))
             return false;
+    // x through TMA stores unless accumulating (or out is not TMA-addressable)
+    const int tma_store =
+        !acc && encode_lines_map(&maps.map[4], out, int(sizeof(T)), L.inner, L.n, outer, CK_SG,
+                                 CK_BOX);
     const size_t smem = LY::bytes(C);
     auto kern = k_chunk_cluster<T, CM>;
     const void *kp = reinterpret_cast<const void *>(kern);
@@ -400,7 +404,7 @@ static bool launch_chunk_cluster_cm(const T *a, const T *b, const T *c, const T 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, out, acc, L, int(nstrips),
-                                             device_status_word());
+                                             tma_store, device_status_word());
     if (e != cudaSuccess) {
         note_cuda_error(e);
         cudaGetLastError();
