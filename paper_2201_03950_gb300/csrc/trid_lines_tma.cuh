@@ -116,7 +116,10 @@ struct LinesTmaLayout {
 
 // nsys systems of n rows, system s at [s * n, s * n + n) of every array;
 // b == nullptr means a unit diagonal.  M rows per thread; a stage holds SPS
-// systems, and the NTEAM / SPS groups of SPS teams take the stages in turn.
+// systems, and the NG = NTEAM / SPS groups of SPS teams take the batches in
+// turn (batch k: stage k % stages, group k % NG).  The host keeps stages a
+// multiple of NG, so every stage always serves the same group and no group
+// ever waits on a stage's full barrier more than one phase ahead.
 // Requirements (host): every pointer 16-byte aligned, n % 4 == 0 (FP32),
 // n <= M * 32 * TW.
 // SWZ (rows of M * sizeof(T) = 32 or 64 bytes, n % M == 0, every system's

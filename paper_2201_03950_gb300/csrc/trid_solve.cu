@@ -304,8 +304,16 @@ static bool launch_lines_tma_tw(const float *a, const float *b, const float *c, 
     if (!di) return false;
     const int n = int(L.n);
     const int narr = b ? 4 : 3;
+    // With NG > 1 team groups taking batches in turn, every stage must always
+    // serve the same group (stages a multiple of NG, batch k in stage k %
+    // stages, group k % NG): a group that could wait on a stage another group
+    // uses might wait two phases ahead of the stage's barrier, which the
+    // parity wait reports as complete, and read another batch's data.
+    constexpr int NG = LY::NTEAM / SPS;
     int stages = 6;
-    while (stages > 2 && LY::bytes(n, narr, stages) > size_t(di->max_smem_optin)) --stages;
+    while (stages > NG && LY::bytes(n, narr, stages) > size_t(di->max_smem_optin)) --stages;
+    stages -= stages % NG;
+    if (stages < NG) return false;
     const size_t smem = LY::bytes(n, narr, stages);
     if (smem > size_t(di->max_smem_optin)) return false;
     TmaSet maps{};  // used by the swizzled variant only

@@ -114,3 +114,26 @@ def test_matches_multipass_path_at_4096sq():
     rows = [slice(k * n, (k + 1) * n) for k in idx]
     ref = oracle.thomas_lines(*(np.stack([v[s] for s in rows]) for v in (a, b, c, d)))
     assert normwise(xs, ref) <= TOL
+
+
+def test_many_batches_every_system_checked():
+    """8192 systems of 4096 rows (two warp teams per block taking the batches
+    in turn), solved three times: the residual of every system, each time.
+    Guards the stage ring's invariant that a stage always serves the same
+    team group (a group waiting on another group's stage could read a batch
+    that is not yet there)."""
+    n, nsys = 4096, 8192
+    a, b, c, d = system(n, nsys, seed=77)
+    ta, tb, tc, td0 = (torch.from_numpy(v).cuda() for v in (a, b, c, d))
+    A, B, C, D = (t.view(nsys, n).double() for t in (ta, tb, tc, td0))
+    scale = (A.abs() + B.abs() + C.abs()).max()
+    for _ in range(3):
+        td = td0.clone()
+        trid.solve(ta, tb, tc, td, (n, nsys), 0)
+        torch.cuda.synchronize()
+        X = td.view(nsys, n).double()
+        r = B * X - D
+        r[:, 1:] += A[:, 1:] * X[:, :-1]
+        r[:, :-1] += C[:, :-1] * X[:, 1:]
+        per_sys = r.abs().amax(dim=1) / (scale * X.abs().amax(dim=1) + D.abs().amax(dim=1))
+        assert per_sys.max().item() <= 8 * n * float(np.finfo(np.float32).eps)
