@@ -142,7 +142,7 @@ def thomas_lines(a, b, c, d, lib=None) -> np.ndarray:
     lib = lib or load()
     a, b, c, d = map(_f64, (a, b, c, d))
     nsys, n = d.shape
-    x = np.empty_like(d)
+    x = np.full_like(d, np.nan)  # a row the solver skips stays NaN
     _check(lib.orc_thomas_lines(nsys, n, _p(a), _p(b), _p(c), _p(d), _p(x)), "thomas_lines")
     return x
 

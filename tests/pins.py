@@ -294,6 +294,27 @@ def pin_varlen(lib, tol=1e-12):
     return worst <= tol, worst
 
 
+def pin_lines(lib, tol=1e-12):
+    """Batch of contiguous systems (rows of a [nsys, n] array, the checker of
+    the full-size sampled GPU tests): every row against LAPACK on its own dense
+    matrix, with NaN planted in each row's unread a_0 and c_{n-1}.  Shapes
+    with nsys != n and several rows, so a wrong row offset or length shows."""
+    worst = 0.0
+    for nsys, n in ((1, 5), (3, 1), (4, 7), (7, 4), (5, 33), (9, 64)):
+        a, b, c, d = inputs.dominant_system((nsys * n,), seed=300 + 7 * nsys + n,
+                                            dtype=np.float64)
+        a, b, c, d = (v.reshape(nsys, n).copy() for v in (a, b, c, d))
+        a[:, 0] = np.nan
+        c[:, -1] = np.nan
+        x = oracle.thomas_lines(a, b, c, d, lib=lib)
+        if x.shape != (nsys, n):
+            return False, float("inf")
+        for k in range(nsys):
+            ref = np.linalg.solve(dense_matrix(a[k], b[k], c[k]), d[k])
+            worst = max(worst, rel(x[k], ref) if np.all(np.isfinite(x[k])) else float("inf"))
+    return worst <= tol, worst
+
+
 def pin_adjoint(lib, tol=1e-7):
     """Adjoint: g_d against LAPACK on A^T (tight), the dot-product identity,
     and g_a, g_b, g_c, g_d against central differences of L = <g, x(a,b,c,d)>."""
@@ -489,5 +510,5 @@ def pin_adi2v_grad(lib, tol=1e-6):
 
 
 ALL_PINS = [pin_lapack, pin_dense_general, pin_exact_rational, pin_toeplitz, pin_manufactured,
-            pin_mesh, pin_adi_eigenmode, pin_adi_dense, pin_varlen, pin_adjoint, pin_adi2v,
+            pin_mesh, pin_adi_eigenmode, pin_adi_dense, pin_varlen, pin_lines, pin_adjoint, pin_adi2v,
             pin_adi2v_grad]

@@ -23,6 +23,12 @@ MUTANTS = [
     ("pcr_rounds", "while (((int64_t)1 << P) < n) ++P;", "while (((int64_t)2 << P) < n) ++P;"),
     ("tiled_dropped_term", "ah[i] = ah[i] - ch[i] * ah[i + 1];", "ah[i] = ah[i];"),
     ("tiled_reduced_diag", "rb[2 * k] = 1.0 - ch[s] * ah[s + 1];", "rb[2 * k] = 1.0;"),
+    ("lines_row_offset", "int rc = orc_thomas(n, a + k * n, b + k * n, c + k * n, d + k * n, x + k * n);",
+     "int rc = orc_thomas(n, a + k, b + k * n, c + k * n, d + k * n, x + k * n);"),
+    ("lines_row_length", "int rc = orc_thomas(n, a + k * n, b + k * n, c + k * n, d + k * n, x + k * n);",
+     "int rc = orc_thomas(n - 1, a + k * n, b + k * n, c + k * n, d + k * n, x + k * n);"),
+    ("lines_row_count", "for (int64_t k = 0; k < nsys; ++k) {\n        int rc = orc_thomas(n,",
+     "for (int64_t k = 0; k + 1 < nsys; ++k) {\n        int rc = orc_thomas(n,"),
     ("mesh_accumulate", "if (accumulate) out[p] += lx[i]; else out[p] = lx[i];", "out[p] = lx[i];"),
     ("adi_stencil_centre", "dd[p] = lambda * (s - 2.0 * ndim * u[p]);", "dd[p] = lambda * (s - ndim * u[p]);"),
     ("adi_operator_diag", "lb[i] = bnd ? 1.0 : 1.0 + 2.0 * lambda;", "lb[i] = bnd ? 1.0 : 1.0 + lambda;"),
