@@ -28,7 +28,11 @@
  *   - No exception, abort() or exit() crosses this ABI.
  *   - Every call may be captured into a CUDA graph, EXCEPT the first call on a
  *     device (which queries device attributes) and calls that need to grow
- *     the library's scratch pool (see trid_solve_batch).
+ *     the library's scratch pool (see trid_solve_batch).  trid_init does both
+ *     ahead of time, so that every later call can be captured.
+ *   - The library caches per-device state (attributes, kernel limits, the
+ *     pool, device addresses).  Call trid_finalize before cudaDeviceReset on
+ *     a device that the library has used.
  */
 #ifndef TRID_H_
 #define TRID_H_
@@ -53,6 +57,32 @@ typedef enum {
     TRID_ERR_ALLOC = 5,       /* scratch allocation failed / workspace too small */
     TRID_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up             */
 } trid_status;
+
+/*
+ * Library lifecycle on the current device (not a construct of the paper: it
+ * owns the scratch that the long-system passes of Section 3.1 need when the
+ * caller passes none).
+ *
+ * trid_init(pool_bytes): queries and caches the current device's attributes,
+ *   looks up the device status word and the allocation-free scratch array,
+ *   and makes the library's scratch pool at least pool_bytes bytes (0: leave
+ *   the pool as it is).  Size the pool with trid_solve_workspace_bytes for the
+ *   largest problem to come; trid_solve_batch calls that fit it then never
+ *   allocate, so they may be captured into a CUDA graph.  Allocates with
+ *   cudaMalloc; not capturable itself.  Calling it again only grows the pool.
+ *   Errors: TRID_ERR_CUDA (no usable device), TRID_ERR_UNSUPPORTED (the
+ *   driver lacks tensor-map encoding), TRID_ERR_ALLOC (cudaMalloc failed).
+ * trid_finalize(): synchronises the current device (every stream), frees its
+ *   scratch pool and forgets every cached state of that device.  Later calls
+ *   work as on a fresh device (the first one re-queries the attributes and
+ *   grows the pool again when it needs it).  Call it before cudaDeviceReset.
+ *   Errors: TRID_ERR_CUDA (no device, or the synchronisation reported an
+ *   error, in which case nothing is freed).
+ * Neither is required: without trid_init the first call on a device does the
+ * same set-up lazily, and the pool lives until the process exits.
+ */
+trid_status trid_init(size_t pool_bytes);
+trid_status trid_finalize(void);
 
 /* Human-readable name of a status code (static storage). */
 const char *trid_status_string(trid_status s);
@@ -88,9 +118,14 @@ const char *trid_last_cuda_error(void);
  * strip of 16 systems.  All other long systems (longer, FP64, unaligned) go
  * through the hybrid in several passes, which need scratch of
  * trid_solve_workspace_bytes(...) bytes; this entry point takes it from a
- * library-owned pool, grown with cudaMalloc only when the multi-pass path is
- * taken (that first call must not be inside a stream capture).  Use
- * trid_solve_batch_ws to pass caller-owned scratch instead.
+ * library-owned pool of the current device, grown (device synchronisation,
+ * cudaFree, cudaMalloc) only when the multi-pass path is taken and the pool
+ * is too small: such a call must not be inside a stream capture (pre-size
+ * the pool with trid_init to avoid it).  The pool is one buffer per device,
+ * shared by every stream: multi-pass calls whose work overlaps on the GPU
+ * (different streams, no ordering between them) race on it and may return
+ * wrong results; order them, or give each stream its own scratch through
+ * trid_solve_batch_ws.  trid_finalize frees the pool.
  * No numerical pivoting: the caller guarantees a nonsingular system for
  * which Gaussian elimination without pivoting is stable (e.g. diagonally
  * dominant rows).  An exact zero pivot yields inf/nan, not an error code.
@@ -196,6 +231,9 @@ size_t trid_solve_varlen_workspace_bytes(int64_t nsys);
  *     may return wrong results; order them, e.g. issue them on one stream.
  *   - The array keeps the last call's contents; the solve overwrites every
  *     scratch value before reading it, so nothing needs clearing.
+ *   - The array's device address is cached per device; after a
+ *     cudaDeviceReset it would be stale, so call trid_finalize (which forgets
+ *     it) before resetting a device.
  */
 #define TRID_NOALLOC_SCRATCH_BYTES (32u << 20)
 trid_status trid_solve_batch_noalloc(const void *a, const void *b, const void *c, void *d,
@@ -245,7 +283,6 @@ trid_status trid_get_device_status(trid_stream_t stream);
  */
 trid_status trid_wait_flag(const int *flag, int expect, double timeout_s, trid_stream_t stream);
 
-/* Library version string (static storage). */
 /*
  * Length classes of trid_solve_batch_varlen: systems of up to 248 rows are
  * solved by one warp each, up to team_max rows by a team of 4 warps, up to
@@ -339,6 +376,7 @@ trid_status adi2v_backward(const void *g_uT, void *g_u0, void *g_kappa, void *g_
                            int every, const void *ckpt, size_t ckpt_bytes, trid_dtype dtype,
                            void *workspace, size_t workspace_bytes, trid_stream_t stream);
 
+/* Library version string (static storage). */
 const char *trid_version(void);
 
 #ifdef __cplusplus

@@ -14,6 +14,8 @@ passage of arXiv 2201.03950 (cited in the C source):
 * ``pcr``           -- Algorithm "pcr" (Section 2)
 * ``tiled``         -- tiled Thomas-Thomas / Thomas-PCR hybrid (Section 3.1)
 * ``solve_mesh``    -- systems along one axis of a column-major mesh (Section 2.1)
+* ``solve_mesh_f32`` -- the same in binary32 (the benchmark's like-for-like FP32
+  CPU baseline only; never a parity reference)
 * ``adi``           -- ADI heat diffusion step, Algorithm "adi" (Section 4.1)
 * ``solve_varlen``  -- a batch of systems of different lengths
 * ``adjoint``       -- transpose solve and coefficient gradients of one solve
@@ -66,6 +68,7 @@ def _bind(lib):
         "orc_tiled": [i64, i64, i32, P, P, P, P, P],
         "orc_thomas_lines": [i64, i64, P, P, P, P, P],
         "orc_solve_mesh": [P, P, P, P, P, P, i32, i32, i32],
+        "orc_solve_mesh_f32": [P, P, P, P, P, P, i32, i32],
         "orc_adi": [P, P, i32, f64, i32],
         "orc_solve_varlen": [P, P, P, P, P, P, i64],
         "orc_adjoint": [i64, P, P, P, P, P, P, P, P, P],
@@ -169,6 +172,18 @@ def solve_mesh(a, b, c, d, dims, solve_dim: int, out=None, lib=None) -> np.ndarr
     _check(lib.orc_solve_mesh(_p(a), _p(b), _p(c), _p(d), _p(res), _dims_c(dims), len(dims),
                               solve_dim, int(acc)), "solve_mesh")
     return out if acc else res
+
+
+def solve_mesh_f32(a, b, c, d, dims, solve_dim: int, out=None, lib=None) -> np.ndarray:
+    """``solve_mesh`` in binary32 (x written to ``out`` or a new array)."""
+    lib = lib or load()
+    a, b, c, d = (np.ascontiguousarray(v, dtype=np.float32).reshape(-1) for v in (a, b, c, d))
+    res = np.full_like(d, np.nan) if out is None else out.reshape(-1)  # unwritten stays NaN
+    if res.dtype != np.float32 or not res.flags.c_contiguous:
+        raise TypeError("out must be a contiguous float32 array")
+    _check(lib.orc_solve_mesh_f32(_p(a), _p(b), _p(c), _p(d), _p(res), _dims_c(dims), len(dims),
+                                  solve_dim), "solve_mesh_f32")
+    return res
 
 
 def adi(u, dims, lam: float, nsteps: int, lib=None) -> np.ndarray:

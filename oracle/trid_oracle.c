@@ -315,6 +315,64 @@ out:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Binary32 twin of orc_solve_mesh (Algorithm "thomas" per system, Section    */
+/* 2.1 line enumeration), every operation rounded to float.  It exists only   */
+/* as the like-for-like (FP32) CPU baseline of the benchmark; the FP64        */
+/* routines above remain the reference the GPU path is checked against.      */
+/* ------------------------------------------------------------------------ */
+static int thomas_f32(int64_t n, const float *a, const float *b, const float *c,
+                      const float *d, float *cp, float *dp, float *x)
+{
+    if (b[0] == 0.0f) return -2;
+    dp[0] = d[0] / b[0];
+    cp[0] = (n > 1 ? c[0] : 0.0f) / b[0];
+    for (int64_t i = 1; i < n; ++i) {
+        float ci = (i == n - 1) ? 0.0f : c[i];
+        float den = b[i] - a[i] * cp[i - 1];
+        if (den == 0.0f) return -2;
+        float r = 1.0f / den;
+        dp[i] = r * (d[i] - a[i] * dp[i - 1]);
+        cp[i] = r * ci;
+    }
+    x[n - 1] = dp[n - 1];
+    for (int64_t i = n - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+    return 0;
+}
+
+int orc_solve_mesh_f32(const float *a, const float *b, const float *c, const float *d,
+                       float *out, const int64_t *dims, int ndim, int solve_dim)
+{
+    if (ndim < 1 || ndim > 3 || solve_dim < 0 || solve_dim >= ndim) return -1;
+    int64_t n3[3] = {1, 1, 1};
+    for (int k = 0; k < ndim; ++k) { if (dims[k] < 0) return -1; n3[k] = dims[k]; }
+    int64_t stride[3] = {1, n3[0], n3[0] * n3[1]};
+    int64_t n = n3[solve_dim], st = stride[solve_dim];
+    if (n == 0) return 0;
+    int o1 = (solve_dim == 0) ? 1 : 0;
+    int o2 = (solve_dim == 2) ? 1 : 2;
+    size_t sz = (size_t)n * sizeof(float);
+    float *la = malloc(sz), *lb = malloc(sz), *lc = malloc(sz), *ld = malloc(sz);
+    float *lx = malloc(sz), *cp = malloc(sz), *dp = malloc(sz);
+    int rc = 0;
+    if (!la || !lb || !lc || !ld || !lx || !cp || !dp) { rc = -1; goto out; }
+    for (int64_t j2 = 0; j2 < n3[o2]; ++j2) {
+        for (int64_t j1 = 0; j1 < n3[o1]; ++j1) {
+            int64_t base = j1 * stride[o1] + j2 * stride[o2];
+            for (int64_t i = 0; i < n; ++i) {
+                int64_t p = base + i * st;
+                la[i] = a[p]; lb[i] = b[p]; lc[i] = c[p]; ld[i] = d[p];
+            }
+            rc = thomas_f32(n, la, lb, lc, ld, cp, dp, lx);
+            if (rc) goto out;
+            for (int64_t i = 0; i < n; ++i) out[base + i * st] = lx[i];
+        }
+    }
+out:
+    free(la); free(lb); free(lc); free(ld); free(lx); free(cp); free(dp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* ADI heat diffusion, Section 4.1, Algorithm adi, in delta form:             */
 /*   1. d = lambda * (sum of the 2*ndim axis neighbours - 2*ndim*u) at        */
 /*      interior nodes, d = 0 on boundary nodes (the explicit RHS stencil,    */

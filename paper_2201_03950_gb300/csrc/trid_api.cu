@@ -232,6 +232,25 @@ trid_status pool_reserve(size_t bytes, void **out) {
     return TRID_OK;
 }
 
+// Drops every cached per-device state of device `dev` and frees its pool
+// (the caller has synchronised the device).  Used by trid_finalize.
+static void forget_device(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_ptr[dev]) cudaFree(g_pool_ptr[dev]);
+    g_pool_ptr[dev] = nullptr;
+    g_pool_size[dev] = 0;
+    g_status_ptr[dev] = nullptr;
+    g_info_ok[dev] = false;
+    int k = 0;
+    for (int i = 0; i < g_nocc; ++i)
+        if (g_occ[i].dev != dev) g_occ[k++] = g_occ[i];
+    g_nocc = k;
+    k = 0;
+    for (int i = 0; i < g_ncc; ++i)
+        if (g_ccache[i].dev != dev) g_ccache[k++] = g_ccache[i];
+    g_ncc = k;
+}
+
 int *device_status_word() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
@@ -279,7 +298,37 @@ extern "C" const char *trid_last_cuda_error(void) {
     return e == 0 ? "none" : cudaGetErrorString(cudaError_t(e));
 }
 
-extern "C" const char *trid_version(void) { return "gb300-trid 0.1 (sm_103a)"; }
+extern "C" const char *trid_version(void) { return "gb300-trid 0.2 (sm_103a)"; }
+
+extern "C" trid_status trid_init(size_t pool_bytes) {
+    if (!trid::device_info()) return TRID_ERR_CUDA;
+    if (!trid::device_status_word()) return TRID_ERR_CUDA;
+    if (!trid::noalloc_scratch_ready()) return TRID_ERR_CUDA;
+    if (!trid::encode_lines_map_ready()) return TRID_ERR_UNSUPPORTED;
+    if (pool_bytes > 0) {
+        void *p = nullptr;
+        const trid_status s = trid::pool_reserve(pool_bytes, &p);
+        if (s != TRID_OK) return s;
+    }
+    return TRID_OK;
+}
+
+extern "C" trid_status trid_finalize(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= trid::kMaxDevices) {
+        cudaGetLastError();
+        return TRID_ERR_CUDA;
+    }
+    // work in flight on any stream may still use the pool
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        trid::note_cuda_error(e);
+        return TRID_ERR_CUDA;
+    }
+    trid::forget_device(dev);
+    trid::noalloc_forget_device(dev);
+    return TRID_OK;
+}
 
 extern "C" trid_status trid_get_device_status(trid_stream_t stream) {
     int *w = trid::device_status_word();

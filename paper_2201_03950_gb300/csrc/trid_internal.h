@@ -65,6 +65,12 @@ size_t adi3_batch_ws_bytes(const int64_t *n3, size_t esz, int64_t nb);
 trid_status adi3_batch_run(void *u, int64_t nb, const int64_t *n3, double lam, int nsteps,
                            trid_dtype dtype, void *ws, size_t ws_bytes, cudaStream_t st);
 
+// Allocation-free entry point's fixed array: looks its device address up on
+// the current device (true on success), and forgets the cached address of
+// device `dev` (trid_finalize).
+bool noalloc_scratch_ready();
+void noalloc_forget_device(int dev);
+
 // Record a failed CUDA runtime call (read back by trid_last_cuda_error).
 void note_cuda_error(cudaError_t e);
 // cudaGetLastError() == cudaSuccess after a launch; a failure is recorded.

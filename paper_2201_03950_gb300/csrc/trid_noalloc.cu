@@ -45,6 +45,15 @@ void *scratch_address() {
 
 }  // namespace
 
+namespace trid {
+bool noalloc_scratch_ready() { return scratch_address() != nullptr; }
+void noalloc_forget_device(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_addr[dev] = nullptr;
+}
+}  // namespace trid
+
 extern "C" trid_status trid_solve_batch_noalloc(const void *a, const void *b, const void *c,
                                                 void *d, void *u, const int64_t *dims, int ndim,
                                                 int solve_dim, trid_dtype dtype,

@@ -475,11 +475,13 @@ static trid_status solve_lines(const T *a, const T *b, const T *c, const T *d, T
     const int64_t ntiles = (L.n + TILE_M - 1) / TILE_M;
     const int64_t R = 2 * ntiles;
     const size_t one = align_up(size_t(L.nsys) * size_t(R) * sizeof(T), 256);
-    if (ws_bytes < long_ws_bytes<T>(L.nsys, L.n) || ws == nullptr) return TRID_ERR_ALLOC;
+    // limits of the multi-pass path first, so that a problem no path serves
+    // reports TRID_ERR_UNSUPPORTED whether or not scratch was given
     if (!contig && (ntiles + 7) / 8 > 65535) return TRID_ERR_UNSUPPORTED;  // grid.y limit
     // the kernels' 32-bit thread and line indices
     if (L.nsys * ntiles >= (int64_t(1) << 31) || L.nsys >= (int64_t(1) << 31))
         return TRID_ERR_UNSUPPORTED;
+    if (ws_bytes < long_ws_bytes<T>(L.nsys, L.n) || ws == nullptr) return TRID_ERR_ALLOC;
     T *ra = reinterpret_cast<T *>(ws);
     T *rc = reinterpret_cast<T *>(ws + one);
     T *rd = reinterpret_cast<T *>(ws + 2 * one);

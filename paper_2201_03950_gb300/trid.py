@@ -79,6 +79,8 @@ def _bind(L):
         "trid_status_string": ([i32], ctypes.c_char_p),
         "trid_last_cuda_error": ([], ctypes.c_char_p),
         "trid_version": ([], ctypes.c_char_p),
+        "trid_init": ([sz], i32),
+        "trid_finalize": ([], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -393,3 +395,19 @@ def status_string(code: int) -> str:
 
 def version() -> str:
     return load().trid_version().decode()
+
+
+def init(pool_bytes: int = 0) -> None:
+    """trid_init: set up the current device and make the scratch pool at least
+    ``pool_bytes`` bytes, so later solves that fit it allocate nothing."""
+    st = load().trid_init(int(pool_bytes))
+    if st != 0:
+        raise TridError(st, "trid_init")
+
+
+def finalize() -> None:
+    """trid_finalize: synchronise the current device, free the scratch pool
+    and forget the library's cached state of that device."""
+    st = load().trid_finalize()
+    if st != 0:
+        raise TridError(st, "trid_finalize")

@@ -43,6 +43,8 @@ def dense_matrix(a, b, c):
 def rel(x, ref):
     x = np.asarray(x, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
+    if not np.all(np.isfinite(x)):
+        return float("inf")  # a NaN would slip through max() comparisons
     scale = max(np.max(np.abs(ref)), 1e-300)
     return float(np.max(np.abs(x - ref)) / scale)
 
@@ -202,6 +204,35 @@ def pin_mesh(lib, tol=1e-12):
         worst = max(worst, rel(u - u0, x_ref))
     return worst <= tol, worst
 
+
+def pin_mesh_f32(lib, tol=2e-6):
+    """The binary32 mesh solve (the FP32 CPU baseline): each axis against
+    LAPACK in binary64 on FP32-representable inputs, within a few FP32 ulps
+    (the systems are diagonally dominant, so Thomas is stable), with NaN in
+    every unread first a / last c."""
+    worst = 0.0
+    dims = (6, 5, 7)
+    tot = 210
+    a, b, c, d = (v.astype(np.float64) for v in
+                  inputs.dominant_system((tot,), seed=19, dtype=np.float32))
+    strides = (1, 6, 30)
+    for k in range(3):
+        n, st = dims[k], strides[k]
+        aa = a.copy(); cc = c.copy()
+        x_ref = np.zeros(tot)
+        others = [ax for ax in range(3) if ax != k]
+        for j2 in range(dims[others[1]]):
+            for j1 in range(dims[others[0]]):
+                base = j1 * strides[others[0]] + j2 * strides[others[1]]
+                idx = base + st * np.arange(n)
+                aa[idx[0]] = np.nan
+                cc[idx[-1]] = np.nan
+                x_ref[idx] = np.linalg.solve(dense_matrix(a[idx], b[idx], c[idx]), d[idx])
+        x = oracle.solve_mesh_f32(aa, b, cc, d, dims, k, lib=lib)
+        if x.dtype != np.float32:
+            return False, float("inf")
+        worst = max(worst, rel(x, x_ref))
+    return worst <= tol, worst
 
 def _mu(p, n):
     return -4.0 * math.sin(math.pi * p / (2.0 * (n - 1))) ** 2
@@ -510,5 +541,5 @@ def pin_adi2v_grad(lib, tol=1e-6):
 
 
 ALL_PINS = [pin_lapack, pin_dense_general, pin_exact_rational, pin_toeplitz, pin_manufactured,
-            pin_mesh, pin_adi_eigenmode, pin_adi_dense, pin_varlen, pin_lines, pin_adjoint, pin_adi2v,
+            pin_mesh, pin_mesh_f32, pin_adi_eigenmode, pin_adi_dense, pin_varlen, pin_lines, pin_adjoint, pin_adi2v,
             pin_adi2v_grad]

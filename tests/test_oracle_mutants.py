@@ -29,6 +29,10 @@ MUTANTS = [
      "int rc = orc_thomas(n - 1, a + k * n, b + k * n, c + k * n, d + k * n, x + k * n);"),
     ("lines_row_count", "for (int64_t k = 0; k < nsys; ++k) {\n        int rc = orc_thomas(n,",
      "for (int64_t k = 0; k + 1 < nsys; ++k) {\n        int rc = orc_thomas(n,"),
+    ("f32_forward_sign", "dp[i] = r * (d[i] - a[i] * dp[i - 1]);",
+     "dp[i] = r * (d[i] + a[i] * dp[i - 1]);"),
+    ("f32_line_stride", "for (int64_t i = 0; i < n; ++i) out[base + i * st] = lx[i];",
+     "for (int64_t i = 0; i < n; ++i) out[base + i] = lx[i];"),
     ("mesh_accumulate", "if (accumulate) out[p] += lx[i]; else out[p] = lx[i];", "out[p] = lx[i];"),
     ("adi_stencil_centre", "dd[p] = lambda * (s - 2.0 * ndim * u[p]);", "dd[p] = lambda * (s - ndim * u[p]);"),
     ("adi_operator_diag", "lb[i] = bnd ? 1.0 : 1.0 + 2.0 * lambda;", "lb[i] = bnd ? 1.0 : 1.0 + lambda;"),

@@ -41,13 +41,28 @@ def _call(lib, fn, ta, tb, tc, td, dims, k, dtype_code):
               k, dtype_code, stream)
 
 
-@pytest.mark.parametrize("dims,k,dtype", [((3000, 40), 0, np.float32), ((48, 2100), 1, np.float32),
-                                          ((1500, 30), 0, np.float64), ((200, 4, 600), 2, np.float32)])
-def test_noalloc_matches_trid_solve_batch_twice(lib, dims, k, dtype):
+# (dims, axis, dtype, uses_scratch): the cases marked True are off the
+# one-pass long-system path (FP64, longer than 4096 rows, or a contiguous
+# length that is not a multiple of 4), so they run the multi-pass solve
+# through the fixed array; the others are taken by the one-pass kernels.
+CASES = [((3000, 40), 0, np.float32, False), ((48, 2100), 1, np.float32, False),
+         ((1500, 30), 0, np.float64, True), ((200, 4, 600), 2, np.float32, False),
+         ((5000, 64), 0, np.float32, True), ((64, 5000), 1, np.float32, True),
+         ((1030, 50), 0, np.float32, True)]
+
+
+def _off_one_pass(dims, k, dtype):
+    n = dims[k]
+    return dtype == np.float64 or n > 4096 or (k == 0 and n % 4 != 0)
+
+
+@pytest.mark.parametrize("dims,k,dtype,uses_scratch", CASES)
+def test_noalloc_matches_trid_solve_batch_twice(lib, dims, k, dtype, uses_scratch):
     total = int(np.prod(dims))
     code = 0 if dtype == np.float32 else 1
     need = lib.trid_solve_workspace_bytes((ctypes.c_int64 * len(dims))(*dims), len(dims), k, code)
     assert 0 < need <= lib_max()
+    assert _off_one_pass(dims, k, dtype) == uses_scratch
     for call in range(2):  # two calls in a row share the fixed scratch array
         a, b, c, d = inputs.dominant_system((total,), seed=70 + call, dtype=dtype)
         ta, tb, tc, td = (torch.from_numpy(v).cuda() for v in (a, b, c, d))
@@ -66,11 +81,16 @@ def test_noalloc_rejects_problems_beyond_its_scratch(lib):
     dims = (8192, 4096)  # needs more than the fixed 32 MiB
     need = lib.trid_solve_workspace_bytes((ctypes.c_int64 * 2)(*dims), 2, 0, 0)
     assert need > lib_max()
-    t = torch.zeros(16, device="cuda")  # never touched: rejected on the host
+    # full-size arrays, so that no path the dispatch might take could reach
+    # outside them; the problem is rejected on the host all the same
+    ts = [torch.zeros(dims[0] * dims[1], device="cuda") for _ in range(4)]
     dc = (ctypes.c_int64 * 2)(*dims)
-    p = ctypes.c_void_p(t.data_ptr())
-    st = lib.trid_solve_batch_noalloc(p, p, p, p, None, dc, 2, 0, 0, None)
+    p = [ctypes.c_void_p(t.data_ptr()) for t in ts]
+    st = lib.trid_solve_batch_noalloc(p[0], p[1], p[2], p[3], None, dc, 2, 0, 0, None)
+    torch.cuda.synchronize()
     assert st == 5  # TRID_ERR_ALLOC
+    assert all(int(torch.count_nonzero(t)) == 0 for t in ts)  # nothing written
+    del ts
 
 
 def test_noalloc_short_systems_need_no_scratch(lib):
