@@ -1,25 +1,28 @@
 // trid_adi.cu -- ADI heat-diffusion step (arXiv 2201.03950, Section 4.1,
 // Algorithm "adi") with the coefficients generated inside the kernels.
 //
-// One step, delta form, Dirichlet-zero boundary:
+// One step, delta form, Dirichlet boundary (boundary nodes never change):
 //   d = lambda * (sum of axis neighbours - 2*ndim*u)   (interior; 0 on boundary)
 //   d <- X^{-1} d ; d <- Y^{-1} d ; [d <- Z^{-1} d] ; u <- u + d
 // with X, Y, Z = tridiag(-lambda, 1 + 2 lambda, -lambda) on interior rows and
 // identity rows at the boundary nodes.
 //
-// Schedule of a 3D step (two passes, five mesh-sized arrays of DRAM traffic,
-// the paper's RHS+x+y / z split):
-//   k_adi_plane : stencil RHS + x solve + y solve per z-plane, u -> w
-//                 (a cluster of blocks holds the plane in shared memory)
-//   k_strided   : z solve, u += result          (reads w, u; writes u)
-// 2D steps, and 3D meshes whose plane does not fit the cluster, use
-//   k_adi_x_rhs : stencil RHS + x solve, u -> w
-//   k_strided   : y solve (in place on w, or u += result in 2D)
-//   k_strided   : z solve, u += result  (3D)
+// Schedules of a 3D step, tried in this order:
+//   windowed (trid_adi_window.cuh, FP32, when the operator's inverse decays
+//     below 1/16 ulp within 8 rows): k_adi_xyw (stencil + x solve + windowed
+//     y solve per plane cluster, writes e = Z u + Y^{-1} X^{-1} d) and k_adi_zw
+//     (windowed z solve, u = Z^{-1} e); 4 mesh words per point.
+//   two-pass (trid_adi_2pass.cuh, extents multiples of 16): k_adi_xy and
+//     k_adi_z_ysub, the y solve split by the Section 3.1 tiling across them.
+//   general (any extents <= 256): stencil + x solve (k_adi_x_static or
+//     k_adi_x_rhs), then y and z solves (k_adi_strided_static / k_strided),
+//     the last one accumulating into u.
+// 2D steps use the general schedule without z.
 #include "trid_device.cuh"
 #include "trid_strided.cuh"
 #include "trid_adi_static.cuh"
 #include "trid_adi_2pass.cuh"
+#include "trid_adi_window.cuh"
 #include "../../include/trid.h"
 #include "trid_internal.h"
 
@@ -430,6 +433,146 @@ static trid_status adi_run_2pass(T *u, const int64_t *n3, T lam, int nsteps, cha
     return TRID_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Windowed 3D schedule (trid_adi_window.cuh): FP32, extents nx % 8 == 0,
+// ny % 32 == 0 (one cluster of ny / 32 CTAs per plane, at most 8), nz % 16 ==
+// 0, all <= 256, and an operator whose window truncation stays below 1/16 ulp.
+// Workspace: e (mesh-sized).
+// ---------------------------------------------------------------------------
+struct AdiWPlan {
+    AdiStatics<float, ADI_XM> sx;
+    XFold<float> xf;
+    WinTab<float, WA_W> yw;
+    WinTab<float, WB_W> zw;
+    int G;
+};
+
+static bool adiw_plan(const int64_t *n3, int64_t nb, double lam, AdiWPlan &p) {
+    const int64_t nx = n3[0], ny = n3[1], nz = n3[2];
+    if (nx % 8 != 0 || nx < 8 || nx > 256) return false;
+    if (ny % WA_YT != 0 || ny < WA_YT || ny > 8 * WA_YT) return false;
+    if (nz % WB_ZT != 0 || nz < WB_ZT || nz > 256) return false;
+    if (nz * nb > 65535) return false;
+    if (!adi_static_fill<float, ADI_XM>(p.sx, int(nx), lam)) return false;
+    if (p.sx.rounds != 0) return false;  // the x solve runs the fold alone
+    const double negligible = 1.0 / double(1 << 28);
+    if (win_fill<float, WA_W>(p.yw, int(ny), WA_YT, lam) > negligible) return false;
+    if (win_fill<float, WB_W>(p.zw, int(nz), WB_ZT, lam) > negligible) return false;
+    xfold_fill<float>(p.xf, p.sx);
+    p.G = pow2_at_least((nx + ADI_XM - 1) / ADI_XM);
+    return true;
+}
+
+template <int G>
+static bool launch_xyw(const float *u, float *e, const int64_t *n3, int64_t nb, float lam,
+                       const AdiWPlan &p, cudaStream_t st, bool check_only) {
+    const int C = int(n3[1] / WA_YT);
+    const size_t smem = 2 * size_t(WA_YT) * size_t(n3[0]) * sizeof(float);
+    auto kern = k_adi_xyw<G>;
+    const void *kp = reinterpret_cast<const void *>(kern);
+    if (kernel_blocks_per_sm(kp, 256, smem) < 1) return false;
+    if (cluster_capacity(kp, C, 256, smem) < 1) return false;
+    if (check_only) return true;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(C);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(unsigned(C), unsigned(n3[2] * nb));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t err =
+        cudaLaunchKernelEx(&cfg, kern, u, e, int(n3[0]), int(n3[1]), int(n3[2]), lam, 6.0f * lam,
+                           1.0f + 2.0f * lam, p.sx, p.xf, p.yw);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        note_cuda_error(err);
+        return false;
+    }
+    return true;
+}
+
+static bool launch_xyw_g(const float *u, float *e, const int64_t *n3, int64_t nb, float lam,
+                         const AdiWPlan &p, cudaStream_t st, bool check_only) {
+    switch (p.G) {
+        case 1: return launch_xyw<1>(u, e, n3, nb, lam, p, st, check_only);
+        case 2: return launch_xyw<2>(u, e, n3, nb, lam, p, st, check_only);
+        case 4: return launch_xyw<4>(u, e, n3, nb, lam, p, st, check_only);
+        case 8: return launch_xyw<8>(u, e, n3, nb, lam, p, st, check_only);
+        case 16: return launch_xyw<16>(u, e, n3, nb, lam, p, st, check_only);
+        case 32: return launch_xyw<32>(u, e, n3, nb, lam, p, st, check_only);
+        default: return false;
+    }
+}
+
+// Pass B launch shape: stages and blocks per SM (two blocks with two to four
+// stages when they fit, else one).
+struct ZwShape {
+    int threads, stages, per_sm;
+    size_t smem;
+};
+
+static bool zw_shape(const int64_t *n3, ZwShape &z) {
+    const DeviceInfo *di = device_info();
+    if (!di) return false;
+    const int n = int(n3[2]);
+    z.threads = 32 * (n / WB_ZT) + 32;
+    const size_t stage = (size_t(n) * WB_SG * sizeof(float) + 127) / 128 * 128;
+    auto bytes = [&](int s) { return size_t(s) * (stage + 16); };
+    const size_t optin = size_t(di->max_smem_optin) - 256;
+    z.stages = 0;
+    for (int per = 2; per >= 1 && z.stages == 0; --per) {
+        size_t cap = size_t(di->smem_per_sm) / per - 4096;
+        if (cap > optin) cap = optin;
+        for (int sg = 4; sg >= 2; --sg)
+            if (bytes(sg) <= cap) { z.stages = sg; break; }
+    }
+    if (z.stages == 0) return false;
+    z.smem = bytes(z.stages);
+    z.per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(k_adi_zw), z.threads, z.smem);
+    return z.per_sm >= 1;
+}
+
+static bool launch_zw(const float *e, float *u, const int64_t *n3, int64_t nb, const AdiWPlan &p,
+                      const ZwShape &z, cudaStream_t st) {
+    const DeviceInfo *di = device_info();
+    if (!di) return false;
+    const int64_t nplane = n3[0] * n3[1];
+    TmaSet maps{};
+    if (!encode_lines_map(&maps.map[0], e, int(sizeof(float)), nplane, n3[2], nb, WB_SG))
+        return false;
+    const int64_t nbatch = nplane / WB_SG * nb;
+    const int64_t slots = int64_t(di->sm_count) * z.per_sm;
+    const int64_t grid = nbatch < slots ? nbatch : slots;
+    k_adi_zw<<<dim3(unsigned(grid)), z.threads, z.smem, st>>>(
+        maps, p.zw, u, int(nplane), int(n3[2]), nbatch, z.stages, device_status_word());
+    return launch_ok();
+}
+
+// Runs nsteps windowed steps; `taken` is false (nothing launched) when the
+// problem does not suit the windowed schedule.
+static trid_status adi_run_window(float *u, const int64_t *n3, double lam, int nsteps, char *ws,
+                                  cudaStream_t st, int64_t nb, bool &taken) {
+    taken = false;
+    static thread_local AdiWPlan p;  // large tables: kept off the stack
+    if (!adiw_plan(n3, nb, lam, p)) return TRID_OK;
+    if (!is_aligned16(u) || !is_aligned16(ws)) return TRID_OK;
+    ZwShape z;
+    if (!zw_shape(n3, z)) return TRID_OK;
+    float *e = reinterpret_cast<float *>(ws);
+    if (!launch_xyw_g(u, e, n3, nb, float(lam), p, st, true)) return TRID_OK;
+    taken = true;
+    for (int step = 0; step < nsteps; ++step) {
+        if (!launch_xyw_g(u, e, n3, nb, float(lam), p, st, false)) return TRID_ERR_CUDA;
+        if (!launch_zw(e, u, n3, nb, p, z, st)) return TRID_ERR_CUDA;
+    }
+    return TRID_OK;
+}
+
 template <typename T>
 static trid_status adi_run(T *u, const int64_t *n3, int ndim, T lam, int nsteps, T *w,
                            cudaStream_t st) {
@@ -494,6 +637,12 @@ trid_status adi3_batch_run(void *u, int64_t nb, const int64_t *n3, double lam, i
     if (!ws || ws_bytes < adi3_batch_ws_bytes(n3, esz, nb)) return TRID_ERR_ALLOC;
     if ((reinterpret_cast<uintptr_t>(ws) % 256) != 0) return TRID_ERR_MISALIGNED;
     if (!is_aligned16(u)) return TRID_ERR_MISALIGNED;
+    if (dtype == TRID_F32) {
+        bool taken = false;
+        const trid_status s = adi_run_window(static_cast<float *>(u), n3, lam, nsteps,
+                                             static_cast<char *>(ws), st, nb, taken);
+        if (taken || s != TRID_OK) return s;
+    }
     if (dtype == TRID_F32)
         return adi_run_2pass<float>(static_cast<float *>(u), n3, float(lam), nsteps,
                                     static_cast<char *>(ws), st, nb);
@@ -535,6 +684,12 @@ extern "C" trid_status adi_step(void *u, const int64_t *dims, int ndim, double l
     }
     if (nsteps == 0) return TRID_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (ndim == 3 && dtype == TRID_F32) {
+        bool taken = false;
+        s = adi_run_window(static_cast<float *>(u), n3, lambda, nsteps,
+                           static_cast<char *>(workspace), st, 1, taken);
+        if (taken || s != TRID_OK) return s;
+    }
     if (adi2_eligible(n3, ndim) && is_aligned16(u)) {
         char *ws = static_cast<char *>(workspace);
         if (dtype == TRID_F32)

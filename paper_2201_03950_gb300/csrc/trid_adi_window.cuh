@@ -1,0 +1,426 @@
+// trid_adi_window.cuh -- 3D ADI step (Section 4.1, Algorithm "adi") with the
+// y and z solves computed over windows of the constant operator.
+//
+// The inverse of the ADI operator tridiag(-lambda, 1 + 2 lambda, -lambda)
+// decays geometrically away from its diagonal: Thomas' forward multipliers
+// and back-substitution factors converge to rho = |c*| of the infinite line
+// (0.084 for lambda = 0.1).  A right-hand-side value k rows away from row i
+// moves x_i by about rho^k relative, so when rho^(H+1) is below 2^-28 (1/16
+// of an FP32 ulp; H = 8 for lambda = 0.1) the rows of a tile need only the
+// right-hand side within H rows of the tile: Thomas on the window [tile - H,
+// tile + H] -- physical boundary rows kept exactly, the couplings across the
+// window's two ends dropped -- returns the tile's rows to within that bound.
+// The host computes the bound from the operator and precision (as it does for
+// the early stop of the PCR rounds) and takes this path only when it holds.
+//
+// One step is u <- u + Z^{-1} Y^{-1} X^{-1} d with d the explicit 7-point
+// right-hand side, computed as u <- Z^{-1}(Z u + Y^{-1} X^{-1} d):
+//   pass A (k_adi_xyw): thread-block clusters of ny / 32 CTAs, one per 32-row
+//     y tile, each cluster walking a run of z planes.  Per plane, warps
+//     compute the stencil and Z u of the tile's rows from the planes z - 1,
+//     z, z + 1 they hold in registers and solve x (lane tiles of 8 rows, one
+//     cyclic-reduction fold through warp shuffles, Section 3.1 form), leaving
+//     X^{-1} d in shared memory; after a cluster barrier each column's y
+//     windows (the 8 rows next to the tile in the neighbouring CTAs read
+//     through distributed shared memory) are solved by one thread per 8 rows,
+//     which writes e = Y^{-1} X^{-1} d + Z u.
+//   pass B (k_adi_zw): a producer warp streams [32 x, nz] boxes of e into a
+//     ring of shared-memory stages (TMA, mbarrier completion); one consumer
+//     warp per 16-row z tile solves the tile's z window for the box's 32 lines
+//     and stores u.  Identity rows at z = 0 and nz - 1 carry e through.
+// DRAM per point: A reads u and writes e; B reads e and writes u (4 words).
+#pragma once
+#include "trid_adi_static.cuh"
+
+namespace trid {
+
+constexpr int WIN_H = 8;                  // window rows on each side of a tile
+constexpr int WA_YT = 32;                 // y rows per CTA of pass A
+constexpr int WA_W = WA_YT + 2 * WIN_H;   // y window rows
+constexpr int WB_ZT = 16;                 // z rows per consumer warp of pass B
+constexpr int WB_W = WB_ZT + 2 * WIN_H;   // z window rows
+constexpr int WB_SG = 32;                 // x lines per box of pass B
+
+// Thomas factors of a tile's window, per tile kind (0 first, 1 interior,
+// 2 last, 3 the only tile): forward f_j = F_j d_j + FA_j f_{j-1}, backward
+// x_j = f_j - C_j x_{j+1}.  Window rows outside the line have F = FA = C = 0.
+template <typename T, int W>
+struct WinTab {
+    T F[4][W], FA[4][W], C[4][W];
+};
+
+// Fold factors of the x solve per lane kind (0 first tile of the line,
+// 1 interior tile, 2 last tile, 3 lane beyond the line); the reduced rows of
+// the constant operator are the same for every interior tile.
+template <typename T>
+struct XFold {
+    T fr[4], fae[4], fce[4], xas[4], xcs[4];
+};
+
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float ld_cluster_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T pick4(int k, const T (&v)[4]) {
+    return k == 0 ? v[0] : (k == 1 ? v[1] : (k == 2 ? v[2] : v[3]));
+}
+
+// Thomas over a window held in registers, with the factors of tile kind K
+// (a compile-time index, so every factor is an immediate constant operand):
+// forward over all W rows, backward down to row `lo`.
+template <int K, int W, int lo>
+__device__ __forceinline__ void win_solve_k(float (&v)[W], const WinTab<float, W> &tab) {
+    float f = 0.0f;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        f = fmaf(tab.FA[K][j], f, tab.F[K][j] * v[j]);
+        v[j] = f;
+    }
+    float xv = v[W - 1];
+#pragma unroll
+    for (int j = W - 2; j >= lo; --j) {
+        xv = fmaf(-tab.C[K][j], xv, v[j]);
+        v[j] = xv;
+    }
+}
+
+template <int W, int lo>
+__device__ __forceinline__ void win_solve(float (&v)[W], const WinTab<float, W> &tab, int kind) {
+    switch (kind) {  // uniform across the warp
+        case 0: win_solve_k<0, W, lo>(v, tab); break;
+        case 1: win_solve_k<1, W, lo>(v, tab); break;
+        case 2: win_solve_k<2, W, lo>(v, tab); break;
+        default: win_solve_k<3, W, lo>(v, tab); break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass A.  Grid (ny / 32, nz * nbatch) in clusters of (ny / 32, 1, 1): the
+// cluster is one z plane (meshes stacked along z), CTA t its rows
+// [32 t, 32 t + 32).  256 threads.  In the x phase a group of G lanes (lane g
+// owning x in [8 g, 8 g + 8)) walks a run of consecutive rows with the rows
+// y - 1, y, y + 1 in registers, loading the next row and its z neighbours one
+// row ahead.  In the y phase thread c solves the window of column c.
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(256, 3)
+k_adi_xyw(const float *__restrict__ u, float *__restrict__ e, int nx, int ny, int nz, float lam,
+          float c6, float bz, const __grid_constant__ AdiStatics<float, ADI_XM> sx,
+          const __grid_constant__ XFold<float> xf,
+          const __grid_constant__ WinTab<float, WA_W> yw) {
+    constexpr int M = ADI_XM;
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NGROUP = 8 * (32 / G);                      // lane groups per CTA
+    constexpr int RG = NGROUP >= WA_YT ? 1 : WA_YT / NGROUP;  // rows per group
+    extern __shared__ __align__(16) unsigned char smem_xyw[];
+    float *sd = reinterpret_cast<float *>(smem_xyw);  // [32][nx] X^{-1} d
+    float *sz = sd + WA_YT * nx;                       // [32][nx] Z u
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int g = lane % G;
+    const int r0 = ((tid >> 5) * (32 / G) + lane / G) * RG;  // first row of the group
+    const bool gact = r0 < WA_YT && g * M < nx;
+    const int x0 = g * M;
+    const int t = int(blockIdx.x), ntile = int(gridDim.x);
+    const int z = int(blockIdx.y);
+    const int zl = z % nz;
+    const bool zint = zl > 0 && zl < nz - 1;
+    const int plane = nx * ny;
+    const int y0 = t * WA_YT;
+    const float *ut = u + size_t(z) * size_t(plane) + size_t(y0) * nx + x0;
+    auto ld = [&](int dy, int dz, bool ok, float (&v)[M]) {  // row y0 + dy of plane z + dz
+        if (ok) {
+            load_contig_vec<float, M>(ut + (dz * ny + dy) * nx, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) v[j] = 0.0f;
+        }
+    };
+    const bool yok0 = y0 + r0 - 1 >= 0;
+    float ym[M], uc[M], yp[M], zs[M];
+    ld(r0 - 1, 0, gact && yok0, ym);
+    ld(r0, 0, gact, uc);
+    ld(r0 + 1, 0, gact && y0 + r0 + 1 < ny, yp);
+    {
+        float a[M], b[M];
+        ld(r0, -1, gact && zint, a);
+        ld(r0, 1, gact && zint, b);
+#pragma unroll
+        for (int j = 0; j < M; ++j) zs[j] = a[j] + b[j];
+    }
+    const int rt = sx.real_tiles;
+    const bool firstx = (g == 0), lastx = (g == rt - 1);
+
+#pragma unroll 1
+    for (int i = 0; i < RG; ++i) {
+        const int r = r0 + i;
+        const int y = y0 + r;
+        const bool more = gact && i + 1 < RG;
+        // next row's loads in flight while this row is solved
+        float ny2[M], zm2[M], zp2[M];
+        ld(r + 2, 0, more && y + 2 < ny, ny2);
+        ld(r + 1, -1, more && zint, zm2);
+        ld(r + 1, 1, more && zint, zp2);
+        const bool rowint = gact && zint && y > 0 && y < ny - 1;
+        float d[M];
+        {
+            float zu[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) zu[j] = zint ? fmaf(-lam, zs[j], bz * uc[j]) : uc[j];
+            if (gact) store_contig_vec<float, M>(sz + r * nx + x0, zu);
+        }
+        const float left = __shfl_up_sync(FULL, uc[M - 1], 1, G);
+        const float right = __shfl_down_sync(FULL, uc[0], 1, G);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const float xm = (j == 0) ? left : uc[j - 1];
+            const float xp = (j == M - 1) ? right : uc[j + 1];
+            const float sm = ((xm + xp) + (ym[j] + yp[j])) + zs[j];
+            d[j] = rowint ? fmaf(lam, sm, -c6 * uc[j]) : 0.0f;
+        }
+        if (firstx) d[0] = 0.0f;
+        if (lastx) d[M - 1] = 0.0f;
+        float ds, de;
+        static_tile_reduce<float, M>(sx, d, firstx, lastx, ds, de);
+        {
+            // reduced system of the line's tiles: one fold (its coupling is
+            // below the bound the host checked, so no PCR round follows)
+            const int kd = g == 0 ? 0 : (g < rt - 1 ? 1 : (g == rt - 1 ? 2 : 3));
+            float nds = __shfl_down_sync(FULL, ds, 1, G);
+            if (g + 1 >= G) nds = 0.0f;
+            const float xe =
+                fmaf(-pick4(kd, xf.fce), nds, fmaf(-pick4(kd, xf.fae), ds, pick4(kd, xf.fr) * de));
+            float xprev = __shfl_up_sync(FULL, xe, 1, G);
+            if (g == 0) xprev = 0.0f;
+            const float xs = fmaf(-pick4(kd, xf.xcs), xe, fmaf(-pick4(kd, xf.xas), xprev, ds));
+            static_tile_substitute<float, M>(sx, d, xs, xe);
+        }
+        if (gact) store_contig_vec<float, M>(sd + r * nx + x0, d);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            ym[j] = uc[j];
+            uc[j] = yp[j];
+            yp[j] = ny2[j];
+            zs[j] = zm2[j] + zp2[j];
+        }
+    }
+    // every CTA of the plane has its X^{-1} d tile in shared memory
+    cluster_arrive_release();
+    cluster_wait_acquire();
+
+    const int c = tid;
+    const bool col = c < nx;
+    float v[WA_W];
+    if (col) {
+        if (t > 0) {
+            const uint32_t up = cluster_map(smem_u32(sd + (WA_YT - WIN_H) * nx + c), t - 1);
+#pragma unroll
+            for (int j = 0; j < WIN_H; ++j) v[j] = ld_cluster_f32(up + 4u * uint32_t(j * nx));
+        } else {
+#pragma unroll
+            for (int j = 0; j < WIN_H; ++j) v[j] = 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < WA_YT; ++j) v[WIN_H + j] = sd[j * nx + c];
+        if (t < ntile - 1) {
+            const uint32_t lo = cluster_map(smem_u32(sd + c), t + 1);
+#pragma unroll
+            for (int j = 0; j < WIN_H; ++j)
+                v[WIN_H + WA_YT + j] = ld_cluster_f32(lo + 4u * uint32_t(j * nx));
+        } else {
+#pragma unroll
+            for (int j = 0; j < WIN_H; ++j) v[WIN_H + WA_YT + j] = 0.0f;
+        }
+        win_solve<WA_W, WIN_H>(v, yw, ntile == 1 ? 3 : (t == 0 ? 0 : (t == ntile - 1 ? 2 : 1)));
+    }
+    // this thread's reads of the neighbours' shared memory are consumed
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    if (col) {
+        float *ecol = e + size_t(z) * size_t(plane) + size_t(y0) * nx + c;
+#pragma unroll
+        for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[WIN_H + j] + sz[j * nx + c];
+    }
+    // no CTA leaves while a neighbour may still read its shared memory
+    cluster_wait_acquire();
+}
+
+// ---------------------------------------------------------------------------
+// Pass B.  Persistent blocks of 32 * (nz / 16) consumer threads (one warp per
+// z tile, one lane per x line of the box) + one producer warp.  Boxes are
+// [32 x, nz] of e at (x0, mesh), mesh-major; the output u has the same layout.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(WB_SG * 16 + 32, 2)
+k_adi_zw(const __grid_constant__ TmaSet maps, const __grid_constant__ WinTab<float, WB_W> zw,
+         float *__restrict__ out, int nplane, int n, int64_t nbatch, int stages, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_zw[];
+    __shared__ int abort_flag;
+    const int ntz = n / WB_ZT;
+    const int ncons = 32 * ntz;
+    const size_t stage_bytes = (size_t(n) * WB_SG * sizeof(float) + 127) / 128 * 128;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_zw + stages * stage_bytes);
+    uint64_t *empty = full + stages;
+    const int64_t nbox = nplane / WB_SG;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ntz);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (tid >= ncons) {
+        if (tid == ncons) {
+            const uint32_t tx = uint32_t(n) * WB_SG * sizeof(float);
+            int k = 0;
+            for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x, ++k) {
+                const int s = k % stages;
+                if (k >= stages && !mbar_wait(&empty[s], uint32_t((k / stages) - 1) & 1u, status)) {
+                    *(volatile int *)&abort_flag = 1;
+                    break;
+                }
+                mbar_expect_tx(&full[s], tx);
+                const int mesh = int(bt / nbox);
+                const int x0 = int(bt - int64_t(mesh) * nbox) * WB_SG;
+                tma_load_3d(smem_zw + s * stage_bytes, &maps.map[0], x0, 0, mesh, &full[s]);
+            }
+        }
+        return;
+    }
+
+    const int lane = tid & 31;
+    const int tz = tid >> 5;  // z tile of this warp
+    const int kind = ntz == 1 ? 3 : (tz == 0 ? 0 : (tz == ntz - 1 ? 2 : 1));
+    const int r0 = tz * WB_ZT - WIN_H;  // first window row
+    int k = 0;
+    for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x, ++k) {
+        const int s = k % stages;
+        bool ok = false;
+        if (!*(volatile int *)&abort_flag) {
+            ok = mbar_wait(&full[s], uint32_t(k / stages) & 1u, status);
+            if (!ok) *(volatile int *)&abort_flag = 1;
+        }
+        const float *sb = reinterpret_cast<const float *>(smem_zw + s * stage_bytes);
+        float v[WB_W];
+#pragma unroll
+        for (int j = 0; j < WB_W; ++j) {
+            const int r = r0 + j;  // warp-uniform
+            v[j] = (ok && r >= 0 && r < n) ? sb[r * WB_SG + lane] : 0.0f;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (!ok) continue;
+        win_solve<WB_W, WIN_H>(v, zw, kind);
+        const int mesh = int(bt / nbox);
+        const int x0 = int(bt - int64_t(mesh) * nbox) * WB_SG;
+        float *ob = out + (size_t(mesh) * n + size_t(tz) * WB_ZT) * size_t(nplane) + x0 + lane;
+#pragma unroll
+        for (int j = 0; j < WB_ZT; ++j) ob[size_t(j) * nplane] = v[WIN_H + j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host: window tables and the truncation bound.
+// ---------------------------------------------------------------------------
+
+// Thomas factors of the window of `tile` (rows tile * tile_rows - H + j,
+// j < W) of a line of n nodes: identity rows at nodes 0 and n - 1,
+// tridiag(-lam, 1 + 2 lam, -lam) inside, the couplings across the window's
+// ends dropped.  `trunc` receives the largest factor by which a dropped
+// coupling can reach a tile row: (lam F_0) * prod FA_1..H at the start and
+// prod of the back-substitution factors over the H + 1 rows after the tile
+// at the end (0 where the window reaches the line's end).
+template <int W>
+inline void win_fill_one(double (&F)[W], double (&FA)[W], double (&C)[W], int n, int tile,
+                         int tile_rows, double lam, double &trunc) {
+    const int y0 = tile * tile_rows - WIN_H;
+    double cprev = 0.0, cfull[W];
+    bool prev = false;
+    for (int j = 0; j < W; ++j) {
+        const int y = y0 + j;
+        if (y < 0 || y >= n) {
+            F[j] = FA[j] = C[j] = cfull[j] = 0.0;
+            cprev = 0.0;
+            prev = false;
+            continue;
+        }
+        const bool ident = (y == 0 || y == n - 1);
+        const double a = (ident || !prev) ? 0.0 : -lam;
+        const double b = ident ? 1.0 : 1.0 + 2.0 * lam;
+        const double c_in = (ident || y + 1 >= n) ? 0.0 : -lam;  // the operator's coupling
+        const double c = (j == W - 1) ? 0.0 : c_in;               // dropped at the window end
+        const double den = b - a * cprev;
+        F[j] = 1.0 / den;
+        FA[j] = -a / den;
+        C[j] = c / den;
+        cfull[j] = c_in / den;
+        cprev = C[j];
+        prev = true;
+    }
+    trunc = 0.0;
+    if (y0 > 0) {  // rows before the window exist: its first row lost a coupling
+        double p = lam * F[0];
+        for (int j = 1; j <= WIN_H; ++j) p *= fabs(FA[j]);
+        trunc = fmax(trunc, p);
+    }
+    if (y0 + W < n) {  // rows after the window exist
+        double p = 1.0;
+        for (int j = W - 1 - WIN_H; j < W; ++j) p *= fabs(cfull[j]);
+        trunc = fmax(trunc, p);
+    }
+}
+
+// Tables of the four tile kinds of a line of n = ntile * tile_rows nodes;
+// returns the largest truncation factor over the kinds that occur.
+template <typename T, int W>
+inline double win_fill(WinTab<T, W> &tab, int n, int tile_rows, double lam) {
+    const int ntile = n / tile_rows;
+    // representative tiles: first, interior, last, only
+    const int rep[4] = {0, ntile >= 3 ? 1 : 0, ntile - 1, 0};
+    const bool occurs[4] = {ntile >= 2, ntile >= 3, ntile >= 2, ntile == 1};
+    double worst = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double F[W], FA[W], C[W], tr = 0.0;
+        win_fill_one<W>(F, FA, C, n, rep[k], tile_rows, lam, tr);
+        for (int j = 0; j < W; ++j) {
+            tab.F[k][j] = T(F[j]);
+            tab.FA[k][j] = T(FA[j]);
+            tab.C[k][j] = T(C[j]);
+        }
+        if (occurs[k]) worst = fmax(worst, tr);
+    }
+    return worst;
+}
+
+// Fold factors of the x solve per lane kind, taken from the per-lane tables.
+template <typename T>
+inline void xfold_fill(XFold<T> &xf, const AdiStatics<T, ADI_XM> &sx) {
+    const int rt = sx.real_tiles;
+    const int rep[4] = {0, rt > 2 ? 1 : 0, rt - 1, rt < 32 ? rt : 31};
+    for (int k = 0; k < 4; ++k) {
+        const int g = rep[k];
+        xf.fr[k] = sx.FR[g];
+        xf.fae[k] = sx.FAE[g];
+        xf.fce[k] = sx.FCE[g];
+        xf.xas[k] = sx.XAS[g];
+        xf.xcs[k] = sx.XCS[g];
+    }
+}
+
+}  // namespace trid

@@ -220,7 +220,11 @@ ADI_SMALL = [((9, 7, 6), 0.1, 3), ((40, 36, 33), 0.1, 10), ((64, 64, 64), 0.1, 5
              ((256, 20, 40), 0.1, 1),
              # two-pass 3D schedule (all extents multiples of 16, nz >= 32)
              ((256, 32, 48), 0.1, 3), ((16, 16, 32), 0.3, 4), ((32, 256, 32), 0.2, 2),
-             ((48, 80, 64), 0.15, 3), ((256, 256, 32), 0.1, 2), ((128, 48, 256), 0.1, 2)]
+             ((48, 80, 64), 0.15, 3), ((256, 256, 32), 0.1, 2), ((128, 48, 256), 0.1, 2),
+             # windowed 3D schedule (FP32: nx % 8, ny % 32, nz % 16, lambda small enough):
+             # three y tile kinds, lanes beyond the x line, one z tile, many z tiles
+             ((256, 96, 64), 0.1, 2), ((24, 128, 16), 0.1, 3), ((200, 160, 80), 0.1, 2),
+             ((8, 32, 32), 0.1, 2), ((64, 64, 256), 0.05, 2)]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
@@ -242,14 +246,15 @@ def test_adi_elementwise(dims, lam, steps, dtype):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
-@pytest.mark.parametrize("dims", [(64, 48, 32), (40, 36, 33), (48, 32)], ids=str)
-def test_adi_nonzero_boundary(dims, dtype):
+@pytest.mark.parametrize("dims,lam", [((64, 48, 32), 0.2), ((40, 36, 33), 0.2), ((48, 32), 0.2),
+                                      ((64, 64, 32), 0.1), ((256, 64, 48), 0.1)], ids=str)
+def test_adi_nonzero_boundary(dims, lam, dtype):
     """Random u everywhere, boundary included: the boundary values must stay
     fixed and enter the neighbours' stencils exactly as in the oracle."""
     rng = np.random.default_rng(7)
     u0 = rng.uniform(-1.0, 1.0, int(np.prod(dims))).astype(dtype)
-    ref = oracle.adi(u0, dims, 0.2, 3)
-    got = run_adi(u0, dims, 0.2, 3, dtype)
+    ref = oracle.adi(u0, dims, lam, 3)
+    got = run_adi(u0, dims, lam, 3, dtype)
     assert normwise(got, ref) <= TOL[dtype]
 
 
