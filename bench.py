@@ -4,13 +4,16 @@
 
 One step = solve(x) + solve(y) + solve(z) + adi_step(1 step), each call timed
 with CUDA events on the launching stream, with d restored from a pristine copy
-and L2 flushed (a 256 MiB write) before every call, outside the events.
+and L2 flushed (a 256 MiB write, then a 256 MiB read, so no dirty line is left
+for the timed call to write back) before every call, outside the events.
 
 Metric: algorithmic bandwidth of the step in GB/s, counting 5 words per
 unknown for a solve (a, b, c, d read; x written -- the paper's convention,
 Table 1) and 4 words per mesh point for the 3D ADI step (the two-pass schedule
-that runs: u read, e = Z u + Y^{-1} X^{-1} d in tile form written; e read,
-u = Z^{-1} e written).
+that runs: u read, e = Z u + Y^{-1} X^{-1} d written; e read, u = Z^{-1} e
+written).  Before each timed call a GPU-side wait (torch.cuda._sleep) follows
+the L2 flush, so that the host has enqueued the call before its start event
+is reached: the events then time the call's kernels, not the host's launch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -81,18 +84,30 @@ def dist_env():
 # nominal FP64 rate of the part (1.25 TFLOP/s); algorithmic work: the Thomas
 # recurrence's 9 operations per unknown (forward: a c*, b - ., 1/m, c r,
 # a d*, d - ., . r; backward: d* - c* x, as a multiply and a subtract).
-FP64_PEAK_TFLOPS = 1.25
-THOMAS_OPS_PER_UNKNOWN = 9
+# Thomas (Algorithm "thomas") per unknown: one division (1 / (b - a c*)) and
+# five multiply-type operations (the pivot, c*, two for d*, one in the back
+# substitution).  With FP64 on GB300 far below FP32, the FP64 solves are
+# bound by these operations; the peak is taken from the device's own rates,
+# measured live (trid_fp64_rates): 6 / (5 / fma_rate + 1 / div_rate).
+THOMAS_MUL_OPS = 5
+THOMAS_DIV_OPS = 1
 
 
-def roofline_obj(dtype, kernel, achieved_gbs, peak, peak_kind, traffic, nbytes, mean_ms):
+def roofline_obj(dtype, kernel, achieved_gbs, peak, peak_kind, traffic, nbytes, mean_ms,
+                 fp64_rates=None):
     if dtype == "f64":
         unknowns = nbytes // (5 * 8)
-        tflops = THOMAS_OPS_PER_UNKNOWN * unknowns / (mean_ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": kernel, "achieved": round(tflops, 4),
-                "peak": FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 rate (fallback: no measured "
-                "FP64 peak)", "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
-                "traffic": traffic, "algorithmic_ops_per_launch": THOMAS_OPS_PER_UNKNOWN * unknowns,
+        fma_g, div_g = fp64_rates
+        ops = THOMAS_MUL_OPS + THOMAS_DIV_OPS
+        peak_gops = ops / (THOMAS_MUL_OPS / fma_g + THOMAS_DIV_OPS / div_g)
+        gops = ops * unknowns / (mean_ms * 1e-3) / 1e9
+        return {"bound": "alu", "kernel": kernel, "achieved": round(gops, 2),
+                "peak": round(peak_gops, 2),
+                "peak_kind": (f"measured FP64 rates of this device (FMA {fma_g:.1f} G/s, "
+                              f"IEEE division {div_g:.1f} G/s; Thomas mix of 5 FMA-type + 1 "
+                              f"division per unknown)"),
+                "unit": "Gop/s", "frac": round(gops / peak_gops, 4), "traffic": traffic,
+                "algorithmic_ops_per_launch": ops * unknowns,
                 "hbm_frac": round(achieved_gbs / peak, 4)}
     return {"bound": "hbm", "kernel": kernel, "achieved": round(achieved_gbs, 1),
             "peak": peak, "peak_kind": f"{peak_kind} (copy, burst)", "unit": "GB/s",
@@ -209,10 +224,26 @@ def run_ours(args):
     tu = torch.from_numpy(u0).to(dev)
     ws = torch.empty(trid.adi_workspace_bytes(DIMS, tdt), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush_rd = torch.zeros(64 << 20, dtype=torch.float32, device=dev)
+
+    class _Flush:
+        """L2 flush between timed calls: a 256 MiB write, then a 256 MiB read,
+        so that the cache holds none of the call's inputs and no dirty lines
+        whose write-back the timed call would pay for."""
+
+        def fill_(self, v):
+            flush.fill_(v)
+            torch.amax(flush_rd)
+
+    flusher = _Flush()
     stream = torch.cuda.current_stream()
 
     names = ["solve_x", "solve_y", "solve_z", "adi_step"]
-    launches_per_step = 3 * 1 + 3  # one kernel per solve; setup, RHS+x+y tile pass, y substitution+z per ADI step
+    # one kernel per solve; the FP32 step runs the windowed ADI schedule (two
+    # kernels), FP64 the two-pass one (setup, RHS + x + y tile pass, y
+    # substitution + z)
+    launches_per_step = 3 + (2 if args.dtype == "f32" else 3)
+    GAP_CYCLES = 100_000  # ~50 us of GPU-side wait while the host enqueues the call
     nbytes = {"solve_x": metrics.solve_bytes(total, esz), "solve_y": metrics.solve_bytes(total, esz),
               "solve_z": metrics.solve_bytes(total, esz),
               "adi_step": metrics.adi_step_bytes(total, esz)}
@@ -221,13 +252,15 @@ def run_ours(args):
         evs = []
         for k in range(3):
             td.copy_(td0)
-            flush.fill_(k + 1)
+            flusher.fill_(k + 1)
+            torch.cuda._sleep(GAP_CYCLES)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             trid.solve(ta, tb, tc, td, DIMS, k, stream=stream)
             e1.record(stream)
             evs.append((names[k], e0, e1))
-        flush.fill_(7)
+        flusher.fill_(7)
+        torch.cuda._sleep(GAP_CYCLES)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         trid.adi_step(tu, DIMS, LAM, 1, ws, stream=stream)
@@ -274,7 +307,8 @@ def run_ours(args):
             times = []
             for it in range(6):
                 td2.copy_(td2_0)
-                flush.fill_(it + 3)
+                flusher.fill_(it + 3)
+                torch.cuda._sleep(GAP_CYCLES)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 trid.solve(ta2, tb2, tc2, td2, dims2, k, stream=stream)
@@ -300,7 +334,8 @@ def run_ours(args):
             times = []
             dc = (ctypes.c_int64 * 3)(*DIMS)
             for it in range(6):
-                flush.fill_(it + 5)
+                flusher.fill_(it + 5)
+                torch.cuda._sleep(GAP_CYCLES)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 st_ = L.trid_solve_batch_adjoint(*(ctypes.c_void_p(t.data_ptr()) for t in
@@ -339,14 +374,16 @@ def run_ours(args):
             uTv = torch.empty_like(u0v)
             fwd_t, bwd_t = [], []
             for it in range(4):
-                flush.fill_(it + 9)
+                flusher.fill_(it + 9)
+                torch.cuda._sleep(GAP_CYCLES)
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record(stream)
                 trid.adi2v_forward(u0v, kv, dv, 0.2, stv, ev, uT=uTv, ckpt=ckv, workspace=wsv,
                                    stream=stream)
                 e1.record(stream)
                 gv2 = 2.0 * (uTv - tv) / nv
-                flush.fill_(it + 10)
+                flusher.fill_(it + 10)
+                torch.cuda._sleep(GAP_CYCLES)
                 e1b = torch.cuda.Event(enable_timing=True)
                 e1b.record(stream)
                 trid.adi2v_backward(gv2, kv, dv, 0.2, stv, ev, ckv, workspace=wsv, stream=stream)
@@ -371,7 +408,8 @@ def run_ours(args):
                 trid.adi2v_backward(gv2, kv, dv, 0.2, stv, ev, ckv, workspace=wsv, stream=cs_)
             gts = []
             for it in range(4):
-                flush.fill_(it + 11)
+                flusher.fill_(it + 11)
+                torch.cuda._sleep(GAP_CYCLES)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 gvg.replay()
@@ -407,7 +445,8 @@ def run_ours(args):
                 ts_ = []
                 for it in range(4):
                     tub.copy_(tub0)
-                    flush.fill_(it + 3)
+                    flusher.fill_(it + 3)
+                    torch.cuda._sleep(GAP_CYCLES)
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
                     trid.adi_step_batched(tub, nbm, bd, 0.1, nst, stream=stream)
@@ -449,7 +488,8 @@ def run_ours(args):
             times = []
             for it in range(6):
                 td3.copy_(td3_0)
-                flush.fill_(it + 9)
+                flusher.fill_(it + 9)
+                torch.cuda._sleep(GAP_CYCLES)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 gv.replay()
@@ -575,7 +615,10 @@ def run_ours(args):
                       "GBps": round(nbytes[n] / (means[n] * 1e-3) / 1e9, 1),
                       "frac": round(nbytes[n] / (means[n] * 1e-3) / 1e9 / peak, 4)}
                   for n in names}
-    dom = max(["solve_x", "solve_y", "solve_z"], key=lambda n: means[n])
+    # the dominant call of the step: the one that takes the most time (FP64:
+    # the slowest solve, whose Thomas operation count defines the ALU roofline)
+    dom = max(names if args.dtype == "f32" else names[:3], key=lambda n: means[n])
+    fp64_rates = trid.fp64_rates(stream) if args.dtype == "f64" else None
     achieved = nbytes[dom] / (means[dom] * 1e-3) / 1e9
     traffic = profiled_traffic(f"{dom}_{args.dtype}_256")
     out = {
@@ -585,7 +628,8 @@ def run_ours(args):
         "data": "synthetic (seeded diagonally dominant coefficients; ADI from 3 sine eigenmodes)",
         "config": {"workload": WORKLOAD, "dims": list(DIMS), "lambda": LAM,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "flushed before every timed call (256 MiB write); inputs 256 MiB per solve",
+                   "l2": "flushed before every timed call (256 MiB write, then a 256 MiB read: no "
+                         "input resident, no dirty lines left); inputs 256 MiB per solve",
                    "timing": "CUDA events per call on the launching stream, summed per step"},
         "per_call": solve_frac,
         "secondary": secondary,
@@ -593,7 +637,7 @@ def run_ours(args):
         "adi_step_ms_graph100": (round(adi_graph_ms, 4) if isinstance(adi_graph_ms, float)
                                  else adi_graph_ms),
         "roofline": roofline_obj(args.dtype, dom, achieved, peak, peak_kind, traffic,
-                                 nbytes[dom], means[dom]),
+                                 nbytes[dom], means[dom], fp64_rates),
         "e2e": None if e2e_val is None else {
             "value": round(e2e_val, 2), "unit": "GB/s", "ms_per_step": round(e2e_step_ms, 3),
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

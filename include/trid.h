@@ -376,6 +376,18 @@ trid_status adi2v_backward(const void *g_uT, void *g_u0, void *g_kappa, void *g_
                            int every, const void *ckpt, size_t ckpt_bytes, trid_dtype dtype,
                            void *workspace, size_t workspace_bytes, trid_stream_t stream);
 
+/*
+ * Measured FP64 rates of the current device (diagnostic; not a construct of
+ * the paper).  On GB300 the FP64 solves are bound by FP64 arithmetic, not by
+ * HBM; their roofline is taken against these rates.  Times, with CUDA events
+ * on `stream`, a grid filling every SM with independent chains of fused
+ * multiply-adds and one of IEEE divisions, and writes the sustained rates in
+ * 10^9 operations per second (an FMA counts as one operation).  Allocates
+ * nothing; synchronises `stream`, so not for use inside a stream capture.  Errors: TRID_ERR_INVALID_ARG (NULL outputs),
+ * TRID_ERR_CUDA.
+ */
+trid_status trid_fp64_rates(double *fma_gops, double *div_gops, trid_stream_t stream);
+
 /* Library version string (static storage). */
 const char *trid_version(void);
 

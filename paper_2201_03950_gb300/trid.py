@@ -80,6 +80,7 @@ def _bind(L):
         "trid_last_cuda_error": ([], ctypes.c_char_p),
         "trid_version": ([], ctypes.c_char_p),
         "trid_init": ([sz], i32),
+        "trid_fp64_rates": ([P, P, P], i32),
         "trid_finalize": ([], i32),
     }
     for name, (args, res) in sigs.items():
@@ -411,3 +412,12 @@ def finalize() -> None:
     st = load().trid_finalize()
     if st != 0:
         raise TridError(st, "trid_finalize")
+
+
+def fp64_rates(stream=None):
+    """trid_fp64_rates: (FMA, division) rates of the current device in 10^9/s."""
+    f, d = ctypes.c_double(), ctypes.c_double()
+    st = load().trid_fp64_rates(ctypes.byref(f), ctypes.byref(d), _stream(stream))
+    if st != 0:
+        raise TridError(st, "trid_fp64_rates")
+    return f.value, d.value
