@@ -441,6 +441,7 @@ static trid_status adi_run_2pass(T *u, const int64_t *n3, T lam, int nsteps, cha
 // ---------------------------------------------------------------------------
 struct AdiWPlan {
     AdiStatics<float, ADI_XM> sx;
+    XTile<float, ADI_XM> xt;
     XFold<float> xf;
     WinTab<float, WA_W> yw;
     WinTab<float, WB_W> zw;
@@ -459,6 +460,7 @@ static bool adiw_plan(const int64_t *n3, int64_t nb, double lam, AdiWPlan &p) {
     if (win_fill<float, WA_W>(p.yw, int(ny), WA_YT, lam) > negligible) return false;
     if (win_fill<float, WB_W>(p.zw, int(nz), WB_ZT, lam) > negligible) return false;
     xfold_fill<float>(p.xf, p.sx);
+    xtile_fill<float>(p.xt, p.sx);
     p.G = pow2_at_least((nx + ADI_XM - 1) / ADI_XM);
     return true;
 }
@@ -474,20 +476,22 @@ static bool launch_xyw(const float *u, float *e, const int64_t *n3, int64_t nb, 
     if (cluster_capacity(kp, C, 256, smem) < 1) return false;
     if (check_only) return true;
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = unsigned(C);
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3(unsigned(C), unsigned(n3[2] * nb));
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     const cudaError_t err =
         cudaLaunchKernelEx(&cfg, kern, u, e, int(n3[0]), int(n3[1]), int(n3[2]), lam, 6.0f * lam,
-                           1.0f + 2.0f * lam, p.sx, p.xf, p.yw);
+                           1.0f + 2.0f * lam, p.xt, p.xf, p.yw);
     if (err != cudaSuccess) {
         cudaGetLastError();
         note_cuda_error(err);
@@ -548,9 +552,24 @@ static bool launch_zw(const float *e, float *u, const int64_t *n3, int64_t nb, c
     const int64_t nbatch = nplane / WB_SG * nb;
     const int64_t slots = int64_t(di->sm_count) * z.per_sm;
     const int64_t grid = nbatch < slots ? nbatch : slots;
-    k_adi_zw<<<dim3(unsigned(grid)), z.threads, z.smem, st>>>(
-        maps, p.zw, u, int(nplane), int(n3[2]), nbatch, z.stages, device_status_word());
-    return launch_ok();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(z.threads));
+    cfg.dynamicSmemBytes = z.smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t err = cudaLaunchKernelEx(&cfg, k_adi_zw, maps, p.zw, u, int(nplane),
+                                               int(n3[2]), nbatch, z.stages, device_status_word());
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        note_cuda_error(err);
+        return false;
+    }
+    return true;
 }
 
 // Runs nsteps windowed steps; `taken` is false (nothing launched) when the

@@ -183,8 +183,8 @@ __device__ __forceinline__ void stage_lane_statics(const AdiStatics<T, AS_M> &st
 
 // Tile pass on the right-hand side only: d (8 rows) -> hatted d, returns the
 // dynamic parts ds, de of the tile's reduced rows.
-template <typename T, int AS_M>
-__device__ __forceinline__ void static_tile_reduce(const AdiStatics<T, AS_M> &s, T (&d)[AS_M],
+template <typename T, int AS_M, typename S>
+__device__ __forceinline__ void static_tile_reduce(const S &s, T (&d)[AS_M],
                                                    bool first, bool last, T &ds, T &de) {
     d[0] = s.F[0] * d[0];
     d[1] = s.F[1] * d[1];
@@ -197,8 +197,8 @@ __device__ __forceinline__ void static_tile_reduce(const AdiStatics<T, AS_M> &s,
     de = d[AS_M - 1];
 }
 
-template <typename T, int AS_M>
-__device__ __forceinline__ void static_tile_substitute(const AdiStatics<T, AS_M> &s, T (&d)[AS_M],
+template <typename T, int AS_M, typename S>
+__device__ __forceinline__ void static_tile_substitute(const S &s, T (&d)[AS_M],
                                                        T xs, T xe) {
 #pragma unroll
     for (int j = 1; j < AS_M - 1; ++j) d[j] = fma(-s.SC[j], xe, fma(-s.SA[j], xs, d[j]));

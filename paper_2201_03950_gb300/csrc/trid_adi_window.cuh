@@ -49,6 +49,27 @@ struct WinTab {
     T F[4][W], FA[4][W], C[4][W];
 };
 
+// The tile-pass multipliers of the x solve (the part of AdiStatics that the
+// fold-only solve reads; a small kernel parameter keeps the launch cheap).
+template <typename T, int AS_M>
+struct XTile {
+    T F[AS_M], G[AS_M], B[AS_M], SA[AS_M], SC[AS_M];
+    T DS0, DS1;
+    int real_tiles;
+};
+
+// Programmatic dependent launch: the next kernel on the stream may be
+// scheduled once every CTA of this one has started; each kernel waits for the
+// previous one to complete (and its memory to be visible) before touching
+// data that kernel produced or reads.  Pointers to such data are not
+// __restrict__: the compiler may otherwise treat them as unchanging for the
+// whole kernel and read them through the non-coherent path or ahead of the
+// wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Fold factors of the x solve per lane kind (0 first tile of the line,
 // 1 interior tile, 2 last tile, 3 lane beyond the line); the reduced rows of
 // the constant operator are the same for every interior tile.
@@ -119,8 +140,8 @@ __device__ __forceinline__ void win_solve(float (&v)[W], const WinTab<float, W> 
 // ---------------------------------------------------------------------------
 template <int G>
 __global__ void __launch_bounds__(256, 3)
-k_adi_xyw(const float *__restrict__ u, float *__restrict__ e, int nx, int ny, int nz, float lam,
-          float c6, float bz, const __grid_constant__ AdiStatics<float, ADI_XM> sx,
+k_adi_xyw(const float *u, float *e, int nx, int ny, int nz, float lam,
+          float c6, float bz, const __grid_constant__ XTile<float, ADI_XM> sx,
           const __grid_constant__ XFold<float> xf,
           const __grid_constant__ WinTab<float, WA_W> yw) {
     constexpr int M = ADI_XM;
@@ -150,6 +171,8 @@ k_adi_xyw(const float *__restrict__ u, float *__restrict__ e, int nx, int ny, in
             for (int j = 0; j < M; ++j) v[j] = 0.0f;
         }
     };
+    pdl_trigger();
+    pdl_wait();  // u is written by the previous kernel on the stream
     const bool yok0 = y0 + r0 - 1 >= 0;
     float ym[M], uc[M], yp[M], zs[M];
     ld(r0 - 1, 0, gact && yok0, ym);
@@ -283,6 +306,8 @@ k_adi_zw(const __grid_constant__ TmaSet maps, const __grid_constant__ WinTab<flo
         }
         fence_mbar_init();
     }
+    pdl_trigger();
+    pdl_wait();  // e is written, and u read, by the previous kernel on the stream
     __syncthreads();
 
     if (tid >= ncons) {
@@ -406,6 +431,17 @@ inline double win_fill(WinTab<T, W> &tab, int n, int tile_rows, double lam) {
         if (occurs[k]) worst = fmax(worst, tr);
     }
     return worst;
+}
+
+template <typename T>
+inline void xtile_fill(XTile<T, ADI_XM> &xt, const AdiStatics<T, ADI_XM> &sx) {
+    for (int j = 0; j < ADI_XM; ++j) {
+        xt.F[j] = sx.F[j]; xt.G[j] = sx.G[j]; xt.B[j] = sx.B[j];
+        xt.SA[j] = sx.SA[j]; xt.SC[j] = sx.SC[j];
+    }
+    xt.DS0 = sx.DS0;
+    xt.DS1 = sx.DS1;
+    xt.real_tiles = sx.real_tiles;
 }
 
 // Fold factors of the x solve per lane kind, taken from the per-lane tables.
