@@ -83,8 +83,24 @@ def test_weak_dominance():
     ta, tb, tc, td = (torch.from_numpy(v).cuda() for v in (a, b, c, d))
     trid.solve(ta, tb, tc, td, dims, k)
     torch.cuda.synchronize()
-    # the condition number grows as the margin shrinks: compare against the
-    # residual bound instead of the well-conditioned tolerance
+    # the condition number grows as the margin shrinks, so the well-
+    # conditioned tolerance does not apply; per system, check the FP32
+    # backward error (normwise residual) and the forward error against
+    # kappa_inf(A) times that backward error bound, both computed here
     x = td.cpu().numpy().astype(np.float64)
-    assert normwise(x, ref) <= 2e-3
     assert np.all(np.isfinite(x))
+    eps = float(np.finfo(np.float32).eps)
+    bwd_bound = 64 * eps
+    n = dims[1]
+    for s in range(dims[0]):
+        idx = s + dims[0] * np.arange(n)
+        A = np.diag(b[idx].astype(np.float64))
+        A[np.arange(1, n), np.arange(n - 1)] = a[idx][1:]
+        A[np.arange(n - 1), np.arange(1, n)] = c[idx][:-1]
+        xs, rs, ds = x[idx], ref[idx], d[idx].astype(np.float64)
+        anorm = np.max(np.sum(np.abs(A), axis=1))
+        resid = np.max(np.abs(A @ xs - ds)) / (anorm * np.max(np.abs(xs)) + np.max(np.abs(ds)))
+        assert resid <= bwd_bound, (s, resid)
+        kappa = anorm * np.max(np.sum(np.abs(np.linalg.inv(A)), axis=1))
+        fwd = np.max(np.abs(xs - rs)) / np.max(np.abs(rs))
+        assert fwd <= kappa * bwd_bound, (s, fwd, kappa)

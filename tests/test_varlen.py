@@ -119,13 +119,14 @@ def test_varlen_empty_and_too_long_rejected_on_host():
         trid.solve_varlen(t, t, t, t, off2, 10_000_000)  # reduced systems do not fit
 
 
-def test_varlen_full_size_config_sampled():
-    """8192 systems, lengths log-uniform in [16, 16384], FP32: sampled systems
-    against the oracle and the residual over every row."""
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+def test_varlen_full_size_config_sampled(dtype):
+    """8192 systems, lengths log-uniform in [16, 16384], FP32 and FP64:
+    sampled systems against the oracle and the residual over every row."""
     lengths = inputs.loguniform_lengths(8192, 16, 16384, seed=0)
     off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
     total = int(off[-1])
-    a, b, c, d = inputs.dominant_system((total,), seed=0, dtype=np.float32)
+    a, b, c, d = inputs.dominant_system((total,), seed=0, dtype=dtype)
     ta, tb, tc, td = (torch.from_numpy(v).cuda() for v in (a, b, c, d))
     td0 = td.clone()
     trid.solve_varlen(ta, tb, tc, td, torch.from_numpy(off).cuda(), 16384)
@@ -139,7 +140,7 @@ def test_varlen_full_size_config_sampled():
         s, e = off[k], off[k + 1]
         ref = oracle.thomas(a[s:e], b[s:e], c[s:e], d[s:e])
         worst = max(worst, per_system_err(x[s:e], ref, [0, e - s]))
-    assert worst <= 1e-5
+    assert worst <= TOL[dtype]
     # residual |A x - d| over all systems, in FP64 with plain torch ops
     A, B, C, D, X = (t.double() for t in (ta, tb, tc, td0, td))
     r = B * X
@@ -150,7 +151,7 @@ def test_varlen_full_size_config_sampled():
     r[1:] += torch.where(first[1:], 0.0, A[1:] * X[:-1])
     r[:-1] += torch.where(last[:-1], 0.0, C[:-1] * X[1:])
     res = ((r - D).abs().max() / ((A.abs() + B.abs() + C.abs()).max() * X.abs().max() + D.abs().max())).item()
-    assert res <= 1e-5
+    assert res <= (1e-5 if dtype == np.float32 else 1e-13)
 
 
 CLASS_EDGES = [248, 249, 503, 504, 505, 1015, 1016, 1017, 2039, 2040, 2041, 4087, 4088, 4089,
