@@ -685,6 +685,7 @@ extern "C" size_t adi_workspace_bytes(const int64_t *dims, int ndim, trid_dtype 
 extern "C" trid_status adi_step(void *u, const int64_t *dims, int ndim, double lambda,
                                 int nsteps, trid_dtype dtype, void *workspace,
                                 size_t workspace_bytes, trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("adi_step");
     int64_t n3[3], total;
     if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
     trid_status s = adi_dims(dims, ndim, n3, total);

@@ -365,6 +365,7 @@ extern "C" trid_status adi2v_forward(const void *u0, void *uT, const void *kappa
                                      void *ckpt, size_t ckpt_bytes, trid_dtype dtype,
                                      void *workspace, size_t workspace_bytes,
                                      trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("adi2v_forward");
     V2Layout l;
     if (!v2_layout(dims, nsteps, every, dtype, l)) return TRID_ERR_INVALID_ARG;
     trid_status s = v2_common(dims, nsteps, every, dtype, lambda, workspace, workspace_bytes,
@@ -389,6 +390,7 @@ extern "C" trid_status adi2v_backward(const void *g_uT, void *g_u0, void *g_kapp
                                       int nsteps, int every, const void *ckpt, size_t ckpt_bytes,
                                       trid_dtype dtype, void *workspace, size_t workspace_bytes,
                                       trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("adi2v_backward");
     V2Layout l;
     if (!v2_layout(dims, nsteps, every, dtype, l)) return TRID_ERR_INVALID_ARG;
     trid_status s = v2_common(dims, nsteps, every, dtype, lambda, workspace, workspace_bytes,

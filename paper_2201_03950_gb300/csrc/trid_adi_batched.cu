@@ -263,6 +263,7 @@ extern "C" trid_status adi_step_batched(void *u, int64_t nbatch, const int64_t *
                                         double lambda, int nsteps, trid_dtype dtype,
                                         void *workspace, size_t workspace_bytes,
                                         trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("adi_step_batched");
     int64_t n3[3];
     if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
     trid_status s = ba_dims(dims, ndim, n3);

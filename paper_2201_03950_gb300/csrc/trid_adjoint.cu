@@ -353,6 +353,7 @@ extern "C" trid_status trid_solve_batch_adjoint(const void *a, const void *b, co
                                                 void *gc, void *gd, const int64_t *dims, int ndim,
                                                 int solve_dim, trid_dtype dtype, void *workspace,
                                                 size_t workspace_bytes, trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("trid_solve_batch_adjoint");
     if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
     Lines L;
     int64_t total;

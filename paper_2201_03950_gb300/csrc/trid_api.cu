@@ -5,7 +5,11 @@
 #include <cudaTypedefs.h>
 
 #include <atomic>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "trid_internal.h"
 
@@ -290,6 +294,21 @@ bool launch_ok() {
     const cudaError_t e = cudaGetLastError();
     note_cuda_error(e);
     return e == cudaSuccess;
+}
+static bool nvtx_enabled() {
+    static const bool on = [] {
+        const char *v = std::getenv("TRID_NVTX");
+        return v != nullptr && std::strcmp(v, "1") == 0;
+    }();
+    return on;
+}
+
+NvtxScope::NvtxScope(const char *name) : on(nvtx_enabled()) {
+    if (on) nvtxRangePushA(name);
+}
+
+NvtxScope::~NvtxScope() {
+    if (on) nvtxRangePop();
 }
 }  // namespace trid
 

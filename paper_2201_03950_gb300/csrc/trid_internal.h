@@ -71,6 +71,15 @@ trid_status adi3_batch_run(void *u, int64_t nb, const int64_t *n3, double lam, i
 bool noalloc_scratch_ready();
 void noalloc_forget_device(int dev);
 
+// Optional NVTX ranges around the compute entry points, for timeline tools
+// (Nsight Systems): on when the environment has TRID_NVTX=1 (read once per
+// process), otherwise the scope costs one branch.
+struct NvtxScope {
+    bool on;
+    explicit NvtxScope(const char *name);
+    ~NvtxScope();
+};
+
 // Record a failed CUDA runtime call (read back by trid_last_cuda_error).
 void note_cuda_error(cudaError_t e);
 // cudaGetLastError() == cudaSuccess after a launch; a failure is recorded.

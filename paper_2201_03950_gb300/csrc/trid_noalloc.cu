@@ -58,6 +58,7 @@ extern "C" trid_status trid_solve_batch_noalloc(const void *a, const void *b, co
                                                 void *d, void *u, const int64_t *dims, int ndim,
                                                 int solve_dim, trid_dtype dtype,
                                                 trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("trid_solve_batch_noalloc");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     // size and argument check first, without touching the device
     size_t need = 0;

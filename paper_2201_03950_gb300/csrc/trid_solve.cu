@@ -638,6 +638,7 @@ extern "C" trid_status trid_solve_batch_ws(const void *a, const void *b, const v
                                            void *u, const int64_t *dims, int ndim,
                                            int solve_dim, trid_dtype dtype, void *workspace,
                                            size_t workspace_bytes, trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("trid_solve_batch_ws");
     Lines L;
     size_t esz;
     trid_status s = check_solve_args(a, b, c, d, u, dims, ndim, solve_dim, dtype, L, esz);
@@ -652,6 +653,7 @@ extern "C" trid_status trid_solve_batch_ws(const void *a, const void *b, const v
 extern "C" trid_status trid_solve_batch(const void *a, const void *b, const void *c, void *d,
                                         void *u, const int64_t *dims, int ndim, int solve_dim,
                                         trid_dtype dtype, trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("trid_solve_batch");
     Lines L;
     size_t esz;
     trid_status s = check_solve_args(a, b, c, d, u, dims, ndim, solve_dim, dtype, L, esz);

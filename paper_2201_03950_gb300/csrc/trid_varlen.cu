@@ -699,6 +699,7 @@ extern "C" trid_status trid_solve_batch_varlen(const void *a, const void *b, con
                                                int64_t nsys, int64_t total, int64_t max_len,
                                                trid_dtype dtype, void *workspace,
                                                size_t workspace_bytes, trid_stream_t stream) {
+    trid::NvtxScope nvtx_scope("trid_solve_batch_varlen");
     return varlen_entry(a, b, c, d, u, offsets, nsys, total, max_len, dtype, workspace,
                         workspace_bytes, stream, nullptr);
 }
@@ -709,6 +710,7 @@ extern "C" trid_status trid_solve_batch_varlen_cfg(const void *a, const void *b,
                                                    trid_dtype dtype, void *workspace,
                                                    size_t workspace_bytes, trid_stream_t stream,
                                                    const trid_varlen_config *cfg) {
+    trid::NvtxScope nvtx_scope("trid_solve_batch_varlen_cfg");
     return varlen_entry(a, b, c, d, u, offsets, nsys, total, max_len, dtype, workspace,
                         workspace_bytes, stream, cfg);
 }
@@ -728,6 +730,7 @@ extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const 
                                             void *workspace, size_t workspace_bytes,
                                             trid_stream_t stream, trid_varlen_config *best,
                                             float *best_ms) {
+    trid::NvtxScope nvtx_scope("trid_varlen_autotune");
     if (!best) return TRID_ERR_INVALID_ARG;
     best->team_max = int32_t(vl_class_max(VL_E1_DEFAULT));
     best->block_max = int32_t(vl_class_max(VL_E2_DEFAULT));

@@ -233,14 +233,51 @@ def solve_varlen(a, b, c, d, offsets, max_len: int, u=None, workspace=None, stre
     return u if u is not None else d
 
 
-def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None):
+def varlen_histogram_key(offsets, dtype) -> str:
+    """Cache key of an uneven batch: the dtype and the number of systems in
+    each power-of-two length bucket (the buckets the planning pass sorts by)."""
+    import numpy as np
+    off = offsets.detach().to("cpu").numpy() if hasattr(offsets, "detach") else np.asarray(offsets)
+    lens = np.diff(off.astype(np.int64))
+    buckets = np.zeros(64, dtype=np.int64)
+    nz = lens[lens > 1]
+    np.add.at(buckets, np.ceil(np.log2(nz)).astype(np.int64), 1)
+    last = int(np.max(np.nonzero(buckets)[0])) + 1 if buckets.any() else 0
+    return f"{'f32' if str(dtype).endswith('float32') else 'f64'}:" + ",".join(
+        str(int(v)) for v in buckets[:last])
+
+
+def _tune_cache_path():
+    import os
+    return os.environ.get("TRID_TUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "gb300-trid", "varlen_tune.json")
+
+
+def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None, cache: bool = True):
     """Time every admissible length-class configuration on this batch (d is
-    not modified) and return (best VarlenConfig, its time in ms)."""
+    not modified) and return (best VarlenConfig, its time in ms).  With
+    ``cache`` the choice is kept in a JSON file (TRID_TUNE_CACHE, else
+    ~/.cache/gb300-trid/varlen_tune.json) keyed by dtype and length histogram;
+    a batch with a known key returns the stored choice (time -1.0) without
+    timing anything."""
+    import json
+    import os
     import torch
     total = d.numel()
     _check_tensors((a, b, c, d), d, total)
     _check_offsets(offsets)
     nsys = offsets.numel() - 1
+    key = varlen_histogram_key(offsets, d.dtype) if cache else None
+    table = {}
+    if cache:
+        try:
+            with open(_tune_cache_path()) as fh:
+                table = json.load(fh)
+        except (OSError, ValueError):
+            table = {}
+        hit = table.get(key)
+        if hit is not None:
+            return VarlenConfig(int(hit["team_max"]), int(hit["block_max"])), -1.0
     L = load()
     ws = torch.empty(max(int(L.trid_varlen_autotune_workspace_bytes(nsys, total, _dtype(d))), 1),
                      dtype=torch.uint8, device=d.device)
@@ -252,6 +289,18 @@ def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None):
                                 ctypes.byref(ms))
     if st != 0:
         raise TridError(st, "trid_varlen_autotune")
+    if cache:
+        table[key] = {"team_max": int(best.team_max), "block_max": int(best.block_max),
+                      "ms": float(ms.value)}
+        path = _tune_cache_path()
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = f"{path}.tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1, sort_keys=True)
+            os.replace(tmp, path)
+        except OSError:
+            pass  # an unwritable cache only costs a re-tune next time
     return best, float(ms.value)
 
 

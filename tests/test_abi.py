@@ -109,3 +109,12 @@ def test_adi_invalid_arguments(lib):
 def test_binding_refuses_missing_library(tmp_path):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         trid.load(str(tmp_path / "missing.so"))
+
+
+def test_varlen_histogram_key_buckets_and_dtype():
+    """The autotuner's cache key: dtype, then systems per ceil-log2 length
+    bucket (lengths 0 and 1 not counted), trailing empty buckets dropped."""
+    import numpy as np
+    off = np.array([0, 1, 3, 7, 8, 16, 33, 33], dtype=np.int64)  # lengths 1,2,4,1,8,17,0
+    assert trid.varlen_histogram_key(off, "torch.float32") == "f32:0,1,1,1,0,1"
+    assert trid.varlen_histogram_key(off, "torch.float64").startswith("f64:")

@@ -189,7 +189,7 @@ def test_varlen_autotune_picks_a_valid_config_and_keeps_d():
     a, b, c, d = inputs.dominant_system((total,), seed=5, dtype=np.float32)
     ta, tb, tc, td = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (a, b, c, d))
     toff = torch.from_numpy(off).cuda()
-    cfg, ms = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()))
+    cfg, ms = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()), cache=False)
     assert (cfg.team_max, cfg.block_max) in CONFIGS
     assert ms > 0.0
     assert np.array_equal(td.cpu().numpy(), d)  # the autotuner works on a copy
@@ -197,6 +197,22 @@ def test_varlen_autotune_picks_a_valid_config_and_keeps_d():
     torch.cuda.synchronize()
     ref = oracle.solve_varlen(a, b, c, d, off)
     assert per_system_err(td.cpu().numpy(), ref, off) <= TOL[np.float32]
+
+
+def test_varlen_autotune_cache_round_trip(tmp_path, monkeypatch):
+    """The tuned choice is stored per (dtype, length histogram) and returned
+    for a batch with the same histogram without timing (time -1)."""
+    monkeypatch.setenv("TRID_TUNE_CACHE", str(tmp_path / "tune.json"))
+    lengths = inputs.loguniform_lengths(200, 16, 9000, seed=12)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    total = int(off[-1])
+    a, b, c, d = inputs.dominant_system((total,), seed=2, dtype=np.float32)
+    ta, tb, tc, td = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (a, b, c, d))
+    toff = torch.from_numpy(off).cuda()
+    cfg1, ms1 = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()))
+    assert ms1 > 0.0 and (tmp_path / "tune.json").exists()
+    cfg2, ms2 = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()))
+    assert ms2 == -1.0 and (cfg2.team_max, cfg2.block_max) == (cfg1.team_max, cfg1.block_max)
 
 
 def test_varlen_invalid_config_rejected():
