@@ -465,12 +465,12 @@ static bool adiw_plan(const int64_t *n3, int64_t nb, double lam, AdiWPlan &p) {
     return true;
 }
 
-template <int G>
+template <int G, int NXC = 0>
 static bool launch_xyw(const float *u, float *e, const int64_t *n3, int64_t nb, float lam,
                        const AdiWPlan &p, cudaStream_t st, bool check_only) {
     const int C = int(n3[1] / WA_YT);
     const size_t smem = 2 * size_t(WA_YT) * size_t(n3[0]) * sizeof(float);
-    auto kern = k_adi_xyw<G>;
+    auto kern = k_adi_xyw<G, NXC>;
     const void *kp = reinterpret_cast<const void *>(kern);
     if (kernel_blocks_per_sm(kp, 256, smem) < 1) return false;
     if (cluster_capacity(kp, C, 256, smem) < 1) return false;
@@ -508,7 +508,9 @@ static bool launch_xyw_g(const float *u, float *e, const int64_t *n3, int64_t nb
         case 4: return launch_xyw<4>(u, e, n3, nb, lam, p, st, check_only);
         case 8: return launch_xyw<8>(u, e, n3, nb, lam, p, st, check_only);
         case 16: return launch_xyw<16>(u, e, n3, nb, lam, p, st, check_only);
-        case 32: return launch_xyw<32>(u, e, n3, nb, lam, p, st, check_only);
+        case 32:
+            return n3[0] == 256 ? launch_xyw<32, 256>(u, e, n3, nb, lam, p, st, check_only)
+                                : launch_xyw<32>(u, e, n3, nb, lam, p, st, check_only);
         default: return false;
     }
 }

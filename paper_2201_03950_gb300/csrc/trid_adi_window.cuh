@@ -138,14 +138,15 @@ __device__ __forceinline__ void win_solve(float (&v)[W], const WinTab<float, W> 
 // y - 1, y, y + 1 in registers, loading the next row and its z neighbours one
 // row ahead.  In the y phase thread c solves the window of column c.
 // ---------------------------------------------------------------------------
-template <int G>
+template <int G, int NXC>  // NXC: nx as a compile-time constant (0: run-time nx)
 __global__ void __launch_bounds__(256, 3)
-k_adi_xyw(const float *u, float *e, int nx, int ny, int nz, float lam,
+k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
           float c6, float bz, const __grid_constant__ XTile<float, ADI_XM> sx,
           const __grid_constant__ XFold<float> xf,
           const __grid_constant__ WinTab<float, WA_W> yw) {
     constexpr int M = ADI_XM;
     constexpr unsigned FULL = 0xffffffffu;
+    const int nx = NXC ? NXC : nx_arg;  // constant row strides when NXC is given
     constexpr int NGROUP = 8 * (32 / G);                      // lane groups per CTA
     constexpr int RG = NGROUP >= WA_YT ? 1 : WA_YT / NGROUP;  // rows per group
     extern __shared__ __align__(16) unsigned char smem_xyw[];
@@ -187,8 +188,11 @@ k_adi_xyw(const float *u, float *e, int nx, int ny, int nz, float lam,
     }
     const int rt = sx.real_tiles;
     const bool firstx = (g == 0), lastx = (g == rt - 1);
+    const int kd = g == 0 ? 0 : (g < rt - 1 ? 1 : (g == rt - 1 ? 2 : 3));
+    const float fr = pick4(kd, xf.fr), fae = pick4(kd, xf.fae), fce = pick4(kd, xf.fce);
+    const float xas = pick4(kd, xf.xas), xcs = pick4(kd, xf.xcs);
 
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < RG; ++i) {
         const int r = r0 + i;
         const int y = y0 + r;
@@ -208,28 +212,31 @@ k_adi_xyw(const float *u, float *e, int nx, int ny, int nz, float lam,
         }
         const float left = __shfl_up_sync(FULL, uc[M - 1], 1, G);
         const float right = __shfl_down_sync(FULL, uc[0], 1, G);
+        if (rowint) {
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            const float xm = (j == 0) ? left : uc[j - 1];
-            const float xp = (j == M - 1) ? right : uc[j + 1];
-            const float sm = ((xm + xp) + (ym[j] + yp[j])) + zs[j];
-            d[j] = rowint ? fmaf(lam, sm, -c6 * uc[j]) : 0.0f;
+            for (int j = 0; j < M; ++j) {
+                const float xm = (j == 0) ? left : uc[j - 1];
+                const float xp = (j == M - 1) ? right : uc[j + 1];
+                const float sm = ((xm + xp) + (ym[j] + yp[j])) + zs[j];
+                d[j] = fmaf(lam, sm, -c6 * uc[j]);
+            }
+            if (firstx) d[0] = 0.0f;
+            if (lastx) d[M - 1] = 0.0f;
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) d[j] = 0.0f;
         }
-        if (firstx) d[0] = 0.0f;
-        if (lastx) d[M - 1] = 0.0f;
         float ds, de;
         static_tile_reduce<float, M>(sx, d, firstx, lastx, ds, de);
         {
             // reduced system of the line's tiles: one fold (its coupling is
             // below the bound the host checked, so no PCR round follows)
-            const int kd = g == 0 ? 0 : (g < rt - 1 ? 1 : (g == rt - 1 ? 2 : 3));
             float nds = __shfl_down_sync(FULL, ds, 1, G);
             if (g + 1 >= G) nds = 0.0f;
-            const float xe =
-                fmaf(-pick4(kd, xf.fce), nds, fmaf(-pick4(kd, xf.fae), ds, pick4(kd, xf.fr) * de));
+            const float xe = fmaf(-fce, nds, fmaf(-fae, ds, fr * de));
             float xprev = __shfl_up_sync(FULL, xe, 1, G);
             if (g == 0) xprev = 0.0f;
-            const float xs = fmaf(-pick4(kd, xf.xcs), xe, fmaf(-pick4(kd, xf.xas), xprev, ds));
+            const float xs = fmaf(-xcs, xe, fmaf(-xas, xprev, ds));
             static_tile_substitute<float, M>(sx, d, xs, xe);
         }
         if (gact) store_contig_vec<float, M>(sd + r * nx + x0, d);
@@ -279,6 +286,21 @@ k_adi_xyw(const float *u, float *e, int nx, int ny, int nz, float lam,
     }
     // no CTA leaves while a neighbour may still read its shared memory
     cluster_wait_acquire();
+}
+
+// Window of a z tile of kind K from the box in shared memory (sb points at
+// the window's first row, column of this lane), then the window solve.  Rows
+// outside the line (before the first tile, after the last) are zero.
+template <int K>
+__device__ __forceinline__ void zw_load_solve(float (&v)[WB_W], const float *col, int r0,
+                                              const WinTab<float, WB_W> &zw) {
+#pragma unroll
+    for (int j = 0; j < WB_W; ++j) {
+        const bool exists = !((K == 0 || K == 3) && j < WIN_H) &&
+                            !((K == 2 || K == 3) && j >= WIN_H + WB_ZT);
+        v[j] = exists ? col[(r0 + j) * WB_SG] : 0.0f;
+    }
+    win_solve_k<K, WB_W, WIN_H>(v, zw);
 }
 
 // ---------------------------------------------------------------------------
@@ -332,7 +354,7 @@ k_adi_zw(const __grid_constant__ TmaSet maps, const __grid_constant__ WinTab<flo
     const int lane = tid & 31;
     const int tz = tid >> 5;  // z tile of this warp
     const int kind = ntz == 1 ? 3 : (tz == 0 ? 0 : (tz == ntz - 1 ? 2 : 1));
-    const int r0 = tz * WB_ZT - WIN_H;  // first window row
+    const int r0 = tz * WB_ZT - WIN_H;  // first window row (negative for the first tile)
     int k = 0;
     for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x, ++k) {
         const int s = k % stages;
@@ -341,17 +363,18 @@ k_adi_zw(const __grid_constant__ TmaSet maps, const __grid_constant__ WinTab<flo
             ok = mbar_wait(&full[s], uint32_t(k / stages) & 1u, status);
             if (!ok) *(volatile int *)&abort_flag = 1;
         }
-        const float *sb = reinterpret_cast<const float *>(smem_zw + s * stage_bytes);
+        const float *col = reinterpret_cast<const float *>(smem_zw + s * stage_bytes) + lane;
         float v[WB_W];
-#pragma unroll
-        for (int j = 0; j < WB_W; ++j) {
-            const int r = r0 + j;  // warp-uniform
-            v[j] = (ok && r >= 0 && r < n) ? sb[r * WB_SG + lane] : 0.0f;
+        switch (ok ? kind : -1) {  // uniform across the warp
+            case 0: zw_load_solve<0>(v, col, r0, zw); break;
+            case 1: zw_load_solve<1>(v, col, r0, zw); break;
+            case 2: zw_load_solve<2>(v, col, r0, zw); break;
+            case 3: zw_load_solve<3>(v, col, r0, zw); break;
+            default: break;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (!ok) continue;
-        win_solve<WB_W, WIN_H>(v, zw, kind);
         const int mesh = int(bt / nbox);
         const int x0 = int(bt - int64_t(mesh) * nbox) * WB_SG;
         float *ob = out + (size_t(mesh) * n + size_t(tz) * WB_ZT) * size_t(nplane) + x0 + lane;
