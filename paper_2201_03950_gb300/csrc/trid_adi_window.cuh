@@ -130,6 +130,39 @@ __device__ __forceinline__ void win_solve(float (&v)[W], const WinTab<float, W> 
     }
 }
 
+// Shared-memory rows of pass A are swizzled: 16-byte chunk q of a row sits at
+// chunk q ^ ((q >> 3) & 1), so that the eight lanes of a quarter warp, each
+// reading its own 32-byte piece (chunks 2g, 2g + 1), and the 32 threads of a
+// warp reading one column each, both hit 32 different banks.
+__device__ __forceinline__ int swz_chunk(int q) { return q ^ ((q >> 3) & 1); }
+__device__ __forceinline__ int swz_elem(int x) { return (swz_chunk(x >> 2) << 2) | (x & 3); }
+
+__device__ __forceinline__ void lds8_swz(const float *row, int x0, float (&r)[8]) {
+    const float4 a = *reinterpret_cast<const float4 *>(row + (swz_chunk(x0 >> 2) << 2));
+    const float4 b = *reinterpret_cast<const float4 *>(row + (swz_chunk((x0 >> 2) + 1) << 2));
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+}
+__device__ __forceinline__ void sts8_swz(float *row, int x0, const float (&r)[8]) {
+    *reinterpret_cast<float4 *>(row + (swz_chunk(x0 >> 2) << 2)) = make_float4(r[0], r[1], r[2], r[3]);
+    *reinterpret_cast<float4 *>(row + (swz_chunk((x0 >> 2) + 1) << 2)) =
+        make_float4(r[4], r[5], r[6], r[7]);
+}
+
+// 16-byte asynchronous global -> shared copies (Ampere-style cp.async), one
+// commit group per row of a lane group.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Pass A.  Grid (ny / 32, nz * nbatch) in clusters of (ny / 32, 1, 1): the
 // cluster is one z plane (meshes stacked along z), CTA t its rows
@@ -174,18 +207,29 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     };
     pdl_trigger();
     pdl_wait();  // u is written by the previous kernel on the stream
+    // the z neighbours of every row of the group, all in flight at once:
+    // plane z - 1 lands where X^{-1} d of the row will go, plane z + 1 where
+    // its Z u will go (each lane copies, and later reads, only its own chunks)
+#pragma unroll
+    for (int i = 0; i < RG; ++i) {
+        const int r = r0 + i;
+        if (gact && zint) {
+            const float *src = ut + r * nx;
+            float *dm = sd + r * nx, *dp = sz + r * nx;
+            const int q0 = x0 >> 2;
+            cp_async16(dm + (swz_chunk(q0) << 2), src - ny * nx);
+            cp_async16(dm + (swz_chunk(q0 + 1) << 2), src - ny * nx + 4);
+            cp_async16(dp + (swz_chunk(q0) << 2), src + ny * nx);
+            cp_async16(dp + (swz_chunk(q0 + 1) << 2), src + ny * nx + 4);
+        }
+        cp_async_commit();
+    }
     const bool yok0 = y0 + r0 - 1 >= 0;
-    float ym[M], uc[M], yp[M], zs[M];
+    float ym[M], uc[M], yp[M], yq[M];  // rows y - 1 .. y + 2 of the group's first row
     ld(r0 - 1, 0, gact && yok0, ym);
     ld(r0, 0, gact, uc);
     ld(r0 + 1, 0, gact && y0 + r0 + 1 < ny, yp);
-    {
-        float a[M], b[M];
-        ld(r0, -1, gact && zint, a);
-        ld(r0, 1, gact && zint, b);
-#pragma unroll
-        for (int j = 0; j < M; ++j) zs[j] = a[j] + b[j];
-    }
+    ld(r0 + 2, 0, gact && RG > 1 && y0 + r0 + 2 < ny, yq);
     const int rt = sx.real_tiles;
     const bool firstx = (g == 0), lastx = (g == rt - 1);
     const int kd = g == 0 ? 0 : (g < rt - 1 ? 1 : (g == rt - 1 ? 2 : 3));
@@ -196,19 +240,32 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     for (int i = 0; i < RG; ++i) {
         const int r = r0 + i;
         const int y = y0 + r;
-        const bool more = gact && i + 1 < RG;
-        // next row's loads in flight while this row is solved
-        float ny2[M], zm2[M], zp2[M];
-        ld(r + 2, 0, more && y + 2 < ny, ny2);
-        ld(r + 1, -1, more && zint, zm2);
-        ld(r + 1, 1, more && zint, zp2);
+        // the rows two and three ahead stay in flight while this row is solved
+        float ny3[M];
+        ld(r + 3, 0, gact && i + 2 < RG && y + 3 < ny, ny3);
         const bool rowint = gact && zint && y > 0 && y < ny - 1;
+        // this row's z neighbours have landed (this lane's own copies)
+        if (i == 0) cp_async_wait<RG - 1>();
+        if (i == 1) cp_async_wait<(RG > 1 ? RG - 2 : 0)>();
+        if (i == 2) cp_async_wait<(RG > 2 ? RG - 3 : 0)>();
+        if (i == 3) cp_async_wait<0>();
+        float zs[M];
+        if (gact && zint) {
+            float zp[M];
+            lds8_swz(sd + r * nx, x0, zs);
+            lds8_swz(sz + r * nx, x0, zp);
+#pragma unroll
+            for (int j = 0; j < M; ++j) zs[j] += zp[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) zs[j] = 0.0f;
+        }
         float d[M];
         {
             float zu[M];
 #pragma unroll
             for (int j = 0; j < M; ++j) zu[j] = zint ? fmaf(-lam, zs[j], bz * uc[j]) : uc[j];
-            if (gact) store_contig_vec<float, M>(sz + r * nx + x0, zu);
+            if (gact) sts8_swz(sz + r * nx, x0, zu);
         }
         const float left = __shfl_up_sync(FULL, uc[M - 1], 1, G);
         const float right = __shfl_down_sync(FULL, uc[0], 1, G);
@@ -239,13 +296,13 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             const float xs = fmaf(-xcs, xe, fmaf(-xas, xprev, ds));
             static_tile_substitute<float, M>(sx, d, xs, xe);
         }
-        if (gact) store_contig_vec<float, M>(sd + r * nx + x0, d);
+        if (gact) sts8_swz(sd + r * nx, x0, d);
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             ym[j] = uc[j];
             uc[j] = yp[j];
-            yp[j] = ny2[j];
-            zs[j] = zm2[j] + zp2[j];
+            yp[j] = yq[j];
+            yq[j] = ny3[j];
         }
     }
     // every CTA of the plane has its X^{-1} d tile in shared memory
@@ -254,10 +311,11 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
 
     const int c = tid;
     const bool col = c < nx;
+    const int cs = swz_elem(c);
     float v[WA_W];
     if (col) {
         if (t > 0) {
-            const uint32_t up = cluster_map(smem_u32(sd + (WA_YT - WIN_H) * nx + c), t - 1);
+            const uint32_t up = cluster_map(smem_u32(sd + (WA_YT - WIN_H) * nx + cs), t - 1);
 #pragma unroll
             for (int j = 0; j < WIN_H; ++j) v[j] = ld_cluster_f32(up + 4u * uint32_t(j * nx));
         } else {
@@ -265,9 +323,9 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             for (int j = 0; j < WIN_H; ++j) v[j] = 0.0f;
         }
 #pragma unroll
-        for (int j = 0; j < WA_YT; ++j) v[WIN_H + j] = sd[j * nx + c];
+        for (int j = 0; j < WA_YT; ++j) v[WIN_H + j] = sd[j * nx + cs];
         if (t < ntile - 1) {
-            const uint32_t lo = cluster_map(smem_u32(sd + c), t + 1);
+            const uint32_t lo = cluster_map(smem_u32(sd + cs), t + 1);
 #pragma unroll
             for (int j = 0; j < WIN_H; ++j)
                 v[WIN_H + WA_YT + j] = ld_cluster_f32(lo + 4u * uint32_t(j * nx));
@@ -282,7 +340,7 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     if (col) {
         float *ecol = e + size_t(z) * size_t(plane) + size_t(y0) * nx + c;
 #pragma unroll
-        for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[WIN_H + j] + sz[j * nx + c];
+        for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[WIN_H + j] + sz[j * nx + cs];
     }
     // no CTA leaves while a neighbour may still read its shared memory
     cluster_wait_acquire();
