@@ -265,10 +265,14 @@ trid_status adi_step(void *u, const int64_t *dims, int ndim, double lambda, int 
 size_t adi_workspace_bytes(const int64_t *dims, int ndim, trid_dtype dtype);
 
 /*
- * Device status word: kernels that run a bounded wait, or debug bounds
- * checks, record the first failure here instead of trapping.  This call
- * synchronises `stream`, returns TRID_OK or the recorded failure
- * (TRID_ERR_TIMEOUT, TRID_ERR_INVALID_ARG) and clears the word.
+ * Device status word: kernels that run a bounded wait, or that meet an
+ * invalid entry in a device-side argument (varlen offsets), record the first
+ * failure here instead of trapping.  In the debug build (compiled with
+ * TRID_DEBUG_BOUNDS) the index checks of the hot kernels (line solves, strided
+ * solves, both passes of the windowed ADI step) also record
+ * TRID_ERR_INVALID_ARG, having skipped the out-of-range access.  This call
+ * synchronises `stream`, returns TRID_OK or the first recorded failure
+ * (TRID_ERR_TIMEOUT, TRID_ERR_INVALID_ARG) and clears the word(s).
  */
 trid_status trid_get_device_status(trid_stream_t stream);
 

@@ -197,8 +197,10 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     const int plane = nx * ny;
     const int y0 = t * WA_YT;
     const float *ut = u + size_t(z) * size_t(plane) + size_t(y0) * nx + x0;
+    // elements of u and e (all planes of all meshes): the debug build's bounds
+    [[maybe_unused]] const int64_t total = int64_t(gridDim.y) * plane;
     auto ld = [&](int dy, int dz, bool ok, float (&v)[M]) {  // row y0 + dy of plane z + dz
-        if (ok) {
+        if (ok && TRID_BOUNDS(in_span(ut + (dz * ny + dy) * nx - u, M, total))) {
             load_contig_vec<float, M>(ut + (dz * ny + dy) * nx, v);
         } else {
 #pragma unroll
@@ -213,7 +215,8 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
 #pragma unroll
     for (int i = 0; i < RG; ++i) {
         const int r = r0 + i;
-        if (gact && zint) {
+        if (gact && zint && TRID_BOUNDS(in_span(ut + r * nx - ny * nx - u, M, total) &&
+                                        in_span(ut + r * nx + ny * nx - u, M, total))) {
             const float *src = ut + r * nx;
             float *dm = sd + r * nx, *dp = sz + r * nx;
             const int q0 = x0 >> 2;
@@ -337,7 +340,8 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     }
     // this thread's reads of the neighbours' shared memory are consumed
     asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
-    if (col) {
+    if (col && TRID_BOUNDS(in_span(int64_t(z) * plane + int64_t(y0) * nx + c,
+                                   int64_t(WA_YT - 1) * nx + 1, total))) {
         float *ecol = e + size_t(z) * size_t(plane) + size_t(y0) * nx + c;
 #pragma unroll
         for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[WIN_H + j] + sz[j * nx + cs];
@@ -435,7 +439,11 @@ k_adi_zw(const __grid_constant__ TmaSet maps, const __grid_constant__ WinTab<flo
         if (!ok) continue;
         const int mesh = int(bt / nbox);
         const int x0 = int(bt - int64_t(mesh) * nbox) * WB_SG;
-        float *ob = out + (size_t(mesh) * n + size_t(tz) * WB_ZT) * size_t(nplane) + x0 + lane;
+        const int64_t obase = (int64_t(mesh) * n + int64_t(tz) * WB_ZT) * nplane + x0 + lane;
+        if (!TRID_BOUNDS(in_span(obase, int64_t(WB_ZT - 1) * nplane + 1,
+                                 nbatch / nbox * n * int64_t(nplane))))
+            continue;
+        float *ob = out + obase;
 #pragma unroll
         for (int j = 0; j < WB_ZT; ++j) ob[size_t(j) * nplane] = v[WIN_H + j];
     }

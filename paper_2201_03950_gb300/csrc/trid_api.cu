@@ -349,6 +349,20 @@ extern "C" trid_status trid_finalize(void) {
     return TRID_OK;
 }
 
+namespace trid {
+namespace {
+constexpr int kMaxDbgReaders = 32;
+int (*g_dbg_readers[kMaxDbgReaders])() = {};
+int g_ndbg = 0;
+}  // namespace
+
+// Called from static initialisers of the debug build's translation units.
+int register_dbg_reader(int (*reader)()) {
+    if (g_ndbg < kMaxDbgReaders) g_dbg_readers[g_ndbg++] = reader;
+    return g_ndbg;
+}
+}  // namespace trid
+
 extern "C" trid_status trid_get_device_status(trid_stream_t stream) {
     int *w = trid::device_status_word();
     if (!w) return TRID_ERR_CUDA;
@@ -362,6 +376,11 @@ extern "C" trid_status trid_get_device_status(trid_stream_t stream) {
         if (cudaMemcpyAsync(w, &zero, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return TRID_ERR_CUDA;
+    }
+    // debug build: failed index checks of the kernels (none registered otherwise)
+    for (int i = 0; i < trid::g_ndbg; ++i) {
+        const int v = trid::g_dbg_readers[i]();
+        if (h == 0 && v != 0) h = v;
     }
     return static_cast<trid_status>(h);
 }

@@ -25,6 +25,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "trid_debug.cuh"
+
 namespace trid {
 
 // ---- reciprocal ------------------------------------------------------------

@@ -58,7 +58,7 @@ k_lines(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ 
     const int64_t base = sys * n;
 
     T ra[M], rb[M], rc[M], rd[M];
-    if (active && vec_ok && i0 + M <= n) {
+    if (active && vec_ok && i0 + M <= n && TRID_BOUNDS(base + i0 + M <= nsys * n)) {
         load_contig_vec<T, M>(a + base + i0, ra);
         if (b) load_contig_vec<T, M>(b + base + i0, rb);
         else {
@@ -71,7 +71,7 @@ k_lines(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ 
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             const int64_t i = i0 + j;
-            if (active && i < n) {
+            if (active && i < n && TRID_BOUNDS(base + i < nsys * n)) {
                 ra[j] = a[base + i];
                 rb[j] = b ? b[base + i] : T(1);
                 rc[j] = c[base + i];
@@ -91,7 +91,7 @@ k_lines(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ 
     group_solve<T, G>(as, cs, ds, ae, ce, de, g, xs, xe);
     tile_substitute<T, M>(ra, rc, rd, xs, xe);
     if (!active) return;
-    if (vec_ok && i0 + M <= n) {
+    if (vec_ok && i0 + M <= n && TRID_BOUNDS(base + i0 + M <= nsys * n)) {
         if (accumulate) {
             T ru[M];
             load_contig_vec<T, M>(out + base + i0, ru);
@@ -103,7 +103,7 @@ k_lines(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ 
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             const int64_t i = i0 + j;
-            if (i < n) {
+            if (i < n && TRID_BOUNDS(base + i < nsys * n)) {
                 if (accumulate) out[base + i] += rd[j];
                 else out[base + i] = rd[j];
             }

@@ -99,7 +99,8 @@ k_strided(Coef coef, const T *d, T *out, Lines L, int64_t outer) {
         const Coef cf = coef.shifted(base);
         const T *db = d + base;
         T ra[M], rb[M], rc[M], rd[M];
-        if (active && full) {
+        if (active && full &&
+            TRID_BOUNDS(base + int64_t(i0 + M - 1) * stride < L.nsys * L.n)) {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const int off = (i0 + j) * stride;
@@ -110,7 +111,7 @@ k_strided(Coef coef, const T *d, T *out, Lines L, int64_t outer) {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const int i = i0 + j;
-                if (active && i < n) {
+                if (active && i < n && TRID_BOUNDS(base + int64_t(i) * stride < L.nsys * L.n)) {
                     const int off = i * stride;
                     cf.get(off, i, n, ra[j], rb[j], rc[j]);
                     rd[j] = db[off];
@@ -146,7 +147,9 @@ k_strided(Coef coef, const T *d, T *out, Lines L, int64_t outer) {
         if (active) {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
-                if (full || i0 + j < n) ob[(i0 + j) * stride] = ACC ? rd[j] + ru[j] : rd[j];
+                if ((full || i0 + j < n) &&
+                    TRID_BOUNDS(base + int64_t(i0 + j) * stride < L.nsys * L.n))
+                    ob[(i0 + j) * stride] = ACC ? rd[j] + ru[j] : rd[j];
             }
         }
     }
@@ -290,10 +293,13 @@ k_strided_tma(const __grid_constant__ TmaSet maps, Coef coef, T *out, Lines L, i
         named_barrier(1, NCONS);
         tile_substitute<T, M>(ra, rc, rd, s_xs[w], s_xe[w]);
         if (active) {
-            T *ob = out + (size_t(o) * inner_n + x);
+            const size_t base = size_t(o) * inner_n + x;
+            T *ob = out + base;
 #pragma unroll
             for (int j = 0; j < M; ++j)
-                if (full_tile || i0 + j < n) ob[(i0 + j) * stride] = ACC ? rd[j] + ru[j] : rd[j];
+                if ((full_tile || i0 + j < n) &&
+                    TRID_BOUNDS(base + size_t(i0 + j) * stride < size_t(L.nsys) * size_t(L.n)))
+                    ob[(i0 + j) * stride] = ACC ? rd[j] + ru[j] : rd[j];
         }
     }
 }

@@ -32,7 +32,10 @@ class TridError(RuntimeError):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library ``load()`` opens: the debug build (device-side index checks,
+    ``build.build(debug_bounds=True)``) when TRID_DEBUG_BOUNDS=1, else the
+    release build."""
+    return _build.LIB_DBG if os.environ.get("TRID_DEBUG_BOUNDS") == "1" else _build.LIB
 
 
 def load(path: str | None = None):
@@ -40,7 +43,7 @@ def load(path: str | None = None):
     global _lib
     with _lock:
         if _lib is None or path is not None:
-            p = path or _build.LIB
+            p = path or lib_path()
             if not os.path.exists(p):
                 raise RuntimeError(f"CUDA library {p} is missing: run build() first "
                                    "(there is no CPU fallback)")
