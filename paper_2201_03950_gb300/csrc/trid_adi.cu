@@ -443,7 +443,7 @@ struct AdiWPlan {
     AdiStatics<float, ADI_XM> sx;
     XTile<float, ADI_XM> xt;
     XFold<float> xf;
-    WinTab<float, WA_W> yw;
+    WinSplit ys;
     WinTab<float, WB_W> zw;
     int G;
 };
@@ -457,7 +457,7 @@ static bool adiw_plan(const int64_t *n3, int64_t nb, double lam, AdiWPlan &p) {
     if (!adi_static_fill<float, ADI_XM>(p.sx, int(nx), lam)) return false;
     if (p.sx.rounds != 0) return false;  // the x solve runs the fold alone
     const double negligible = 1.0 / double(1 << 28);
-    if (win_fill<float, WA_W>(p.yw, int(ny), WA_YT, lam) > negligible) return false;
+    if (winsplit_fill(p.ys, int(ny), lam) > negligible) return false;
     if (win_fill<float, WB_W>(p.zw, int(nz), WB_ZT, lam) > negligible) return false;
     xfold_fill<float>(p.xf, p.sx);
     xtile_fill<float>(p.xt, p.sx);
@@ -469,7 +469,8 @@ template <int G, int NXC = 0>
 static bool launch_xyw(const float *u, float *e, const int64_t *n3, int64_t nb, float lam,
                        const AdiWPlan &p, cudaStream_t st, bool check_only) {
     const int C = int(n3[1] / WA_YT);
-    const size_t smem = 2 * size_t(WA_YT) * size_t(n3[0]) * sizeof(float);
+    // X^{-1} d and Z u rows, the two received summaries, the mbarrier
+    const size_t smem = (2 * size_t(WA_YT) + 2) * size_t(n3[0]) * sizeof(float) + 16;
     auto kern = k_adi_xyw<G, NXC>;
     const void *kp = reinterpret_cast<const void *>(kern);
     if (kernel_blocks_per_sm(kp, 256, smem) < 1) return false;
@@ -491,7 +492,7 @@ static bool launch_xyw(const float *u, float *e, const int64_t *n3, int64_t nb, 
     cfg.numAttrs = 2;
     const cudaError_t err =
         cudaLaunchKernelEx(&cfg, kern, u, e, int(n3[0]), int(n3[1]), int(n3[2]), lam, 6.0f * lam,
-                           1.0f + 2.0f * lam, p.xt, p.xf, p.yw);
+                           1.0f + 2.0f * lam, p.xt, p.xf, p.ys, device_status_word());
     if (err != cudaSuccess) {
         cudaGetLastError();
         note_cuda_error(err);

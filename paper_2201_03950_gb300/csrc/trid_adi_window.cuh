@@ -15,15 +15,16 @@
 //
 // One step is u <- u + Z^{-1} Y^{-1} X^{-1} d with d the explicit 7-point
 // right-hand side, computed as u <- Z^{-1}(Z u + Y^{-1} X^{-1} d):
-//   pass A (k_adi_xyw): thread-block clusters of ny / 32 CTAs, one per 32-row
-//     y tile, each cluster walking a run of z planes.  Per plane, warps
-//     compute the stencil and Z u of the tile's rows from the planes z - 1,
-//     z, z + 1 they hold in registers and solve x (lane tiles of 8 rows, one
-//     cyclic-reduction fold through warp shuffles, Section 3.1 form), leaving
-//     X^{-1} d in shared memory; after a cluster barrier each column's y
-//     windows (the 8 rows next to the tile in the neighbouring CTAs read
-//     through distributed shared memory) are solved by one thread per 8 rows,
-//     which writes e = Y^{-1} X^{-1} d + Z u.
+//   pass A (k_adi_xyw): one CTA per (32-row y tile, z plane), the tiles of a
+//     plane forming a thread-block cluster.  Warps compute the stencil and
+//     Z u of the tile's rows (the z neighbours staged in shared memory by
+//     cp.async) and solve x (lane tiles of 8 points, one cyclic-reduction fold
+//     through warp shuffles, Section 3.1 form), leaving X^{-1} d in shared
+//     memory.  The y window solve is split by linearity (WinSplit): each CTA
+//     sends its two neighbours one scalar per column summarising the rows
+//     they need (st.async into their shared memory, counted on an mbarrier),
+//     solves its own rows with zero halos meanwhile, adds the received
+//     summaries' responses and writes e = Y^{-1} X^{-1} d + Z u.
 //   pass B (k_adi_zw): a producer warp streams [32 x, nz] boxes of e into a
 //     ring of shared-memory stages (TMA, mbarrier completion); one consumer
 //     warp per 16-row z tile solves the tile's z window for the box's 32 lines
@@ -56,6 +57,25 @@ struct XTile {
     T F[AS_M], G[AS_M], B[AS_M], SA[AS_M], SC[AS_M];
     T DS0, DS1;
     int real_tiles;
+};
+
+// The y window solve of a 32-row tile split by linearity (window rows 0..7
+// the halo above, 8..39 the tile, 40..47 the halo below; x = X^{-1} d per
+// column):
+//   x_tile = x0 + T h + B b,
+// where x0 is the window solve with both halos zero (Thomas over the tile's
+// rows, the rows below entering only through x_40 = R f_39), h = sum_k Wt_k
+// v_k the forward value that the halo above leaves at window row 7, b = sum_k
+// Wb_k v_{40+k} the value x_40 that the halo below alone produces, T the
+// tile's response to a unit forward value at row 7 and B its response to a
+// unit x_40.  A CTA computes h and b for its neighbours from its own rows and
+// sends them one scalar per column, so no CTA reads another's rows.  Per tile
+// kind (0 first, 1 interior, 2 last, 3 only); halves that do not exist are 0.
+struct WinSplit {
+    float F[4][WA_YT], FA[4][WA_YT], C[4][WA_YT];  // window rows 8..39
+    float R[4];
+    float T[4][WA_YT], B[4][WA_YT];
+    float Wt[4][WIN_H], Wb[4][WIN_H];
 };
 
 // Programmatic dependent launch: the next kernel on the stream may be
@@ -96,6 +116,17 @@ __device__ __forceinline__ float ld_cluster_f32(uint32_t addr) {
     return v;
 }
 
+// Store to the shared memory of another CTA of the cluster; the bytes count
+// towards the transaction count of an mbarrier in that CTA.
+__device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];"
+                 ::"r"(addr), "f"(v), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ T pick4(int k, const T (&v)[4]) {
     return k == 0 ? v[0] : (k == 1 ? v[1] : (k == 2 ? v[2] : v[3]));
@@ -127,6 +158,33 @@ __device__ __forceinline__ void win_solve(float (&v)[W], const WinTab<float, W> 
         case 1: win_solve_k<1, W, lo>(v, tab); break;
         case 2: win_solve_k<2, W, lo>(v, tab); break;
         default: win_solve_k<3, W, lo>(v, tab); break;
+    }
+}
+
+// The tile's part of the split window solve for kind K: Thomas over the 32
+// tile rows with zero halos (x_40 = R f_39).
+template <int K>
+__device__ __forceinline__ void tile_own_solve(float (&v)[WA_YT], const WinSplit &ys) {
+    float f = 0.0f;
+#pragma unroll
+    for (int j = 0; j < WA_YT; ++j) {
+        f = fmaf(ys.FA[K][j], f, ys.F[K][j] * v[j]);
+        v[j] = f;
+    }
+    float xv = ys.R[K] * f;
+#pragma unroll
+    for (int j = WA_YT - 1; j >= 0; --j) {
+        xv = fmaf(-ys.C[K][j], xv, v[j]);
+        v[j] = xv;
+    }
+}
+template <int K>
+__device__ __forceinline__ void tile_halo_add(float (&v)[WA_YT], const WinSplit &ys, float h,
+                                              float b) {
+#pragma unroll
+    for (int j = 0; j < WA_YT; ++j) {
+        if (K == 1 || K == 2) v[j] = fmaf(ys.T[K][j], h, v[j]);
+        if (K == 0 || K == 1) v[j] = fmaf(ys.B[K][j], b, v[j]);
     }
 }
 
@@ -168,15 +226,16 @@ __device__ __forceinline__ void cp_async_wait() {
 // cluster is one z plane (meshes stacked along z), CTA t its rows
 // [32 t, 32 t + 32).  256 threads.  In the x phase a group of G lanes (lane g
 // owning x in [8 g, 8 g + 8)) walks a run of consecutive rows with the rows
-// y - 1, y, y + 1 in registers, loading the next row and its z neighbours one
-// row ahead.  In the y phase thread c solves the window of column c.
+// y - 1, y, y + 1 in registers, loading the rows ahead.  In the y phase thread
+// c handles column c: the halo summaries for the neighbours, its own rows'
+// window solve, the received summaries' responses, the store of e.
 // ---------------------------------------------------------------------------
 template <int G, int NXC>  // NXC: nx as a compile-time constant (0: run-time nx)
 __global__ void __launch_bounds__(256, 3)
 k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
           float c6, float bz, const __grid_constant__ XTile<float, ADI_XM> sx,
-          const __grid_constant__ XFold<float> xf,
-          const __grid_constant__ WinTab<float, WA_W> yw) {
+          const __grid_constant__ XFold<float> xf, const __grid_constant__ WinSplit ys,
+          int *status) {
     constexpr int M = ADI_XM;
     constexpr unsigned FULL = 0xffffffffu;
     const int nx = NXC ? NXC : nx_arg;  // constant row strides when NXC is given
@@ -185,6 +244,9 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     extern __shared__ __align__(16) unsigned char smem_xyw[];
     float *sd = reinterpret_cast<float *>(smem_xyw);  // [32][nx] X^{-1} d
     float *sz = sd + WA_YT * nx;                       // [32][nx] Z u
+    float *rh = sz + WA_YT * nx;  // [nx] h from the tile above
+    float *rb = rh + nx;          // [nx] b from the tile below
+    uint64_t *rbar = reinterpret_cast<uint64_t *>(rb + nx);  // both have landed
     const int tid = threadIdx.x, lane = tid & 31;
     const int g = lane % G;
     const int r0 = ((tid >> 5) * (32 / G) + lane / G) * RG;  // first row of the group
@@ -207,6 +269,12 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             for (int j = 0; j < M; ++j) v[j] = 0.0f;
         }
     };
+    if (tid == 0) {
+        mbar_init(rbar, 1);
+        fence_mbar_init();
+    }
+    // every CTA's mbarrier is initialised before any neighbour sends to it
+    cluster_arrive_relaxed();
     pdl_trigger();
     pdl_wait();  // u is written by the previous kernel on the stream
     // the z neighbours of every row of the group, all in flight at once:
@@ -308,45 +376,66 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             yq[j] = ny3[j];
         }
     }
-    // every CTA of the plane has its X^{-1} d tile in shared memory
-    cluster_arrive_release();
-    cluster_wait_acquire();
-
+    __syncthreads();  // this CTA's X^{-1} d rows are complete
+    const bool has_up = t > 0, has_dn = t < ntile - 1;
+    if (tid == 0) mbar_expect_tx(rbar, uint32_t((has_up ? nx : 0) + (has_dn ? nx : 0)) * 4u);
     const int c = tid;
     const bool col = c < nx;
     const int cs = swz_elem(c);
-    float v[WA_W];
+    const int kind = ntile == 1 ? 3 : (t == 0 ? 0 : (t == ntile - 1 ? 2 : 1));
+    cluster_wait_acquire();  // the neighbours' mbarriers are initialised
     if (col) {
-        if (t > 0) {
-            const uint32_t up = cluster_map(smem_u32(sd + (WA_YT - WIN_H) * nx + cs), t - 1);
+        // the halo summaries this tile's rows give its neighbours
+        if (has_dn) {  // h of the tile below (kind 2 if it is the last, else 1)
+            const bool last = t + 1 == ntile - 1;
+            float h = 0.0f;
 #pragma unroll
-            for (int j = 0; j < WIN_H; ++j) v[j] = ld_cluster_f32(up + 4u * uint32_t(j * nx));
-        } else {
-#pragma unroll
-            for (int j = 0; j < WIN_H; ++j) v[j] = 0.0f;
+            for (int k = 0; k < WIN_H; ++k)
+                h = fmaf(last ? ys.Wt[2][k] : ys.Wt[1][k], sd[(WA_YT - WIN_H + k) * nx + cs], h);
+            st_async_f32(cluster_map(smem_u32(rh + c), t + 1), h,
+                         cluster_map(smem_u32(rbar), t + 1));
         }
+        if (has_up) {  // b of the tile above (kind 0 if it is the first, else 1)
+            const bool first = t - 1 == 0;
+            float b = 0.0f;
 #pragma unroll
-        for (int j = 0; j < WA_YT; ++j) v[WIN_H + j] = sd[j * nx + cs];
-        if (t < ntile - 1) {
-            const uint32_t lo = cluster_map(smem_u32(sd + cs), t + 1);
-#pragma unroll
-            for (int j = 0; j < WIN_H; ++j)
-                v[WIN_H + WA_YT + j] = ld_cluster_f32(lo + 4u * uint32_t(j * nx));
-        } else {
-#pragma unroll
-            for (int j = 0; j < WIN_H; ++j) v[WIN_H + WA_YT + j] = 0.0f;
+            for (int k = 0; k < WIN_H; ++k)
+                b = fmaf(first ? ys.Wb[0][k] : ys.Wb[1][k], sd[k * nx + cs], b);
+            st_async_f32(cluster_map(smem_u32(rb + c), t - 1), b,
+                         cluster_map(smem_u32(rbar), t - 1));
         }
-        win_solve<WA_W, WIN_H>(v, yw, ntile == 1 ? 3 : (t == 0 ? 0 : (t == ntile - 1 ? 2 : 1)));
     }
-    // this thread's reads of the neighbours' shared memory are consumed
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    float v[WA_YT];
+    if (col) {
+#pragma unroll
+        for (int j = 0; j < WA_YT; ++j) v[j] = sd[j * nx + cs];
+        switch (kind) {  // uniform across the CTA
+            case 0: tile_own_solve<0>(v, ys); break;
+            case 1: tile_own_solve<1>(v, ys); break;
+            case 2: tile_own_solve<2>(v, ys); break;
+            default: tile_own_solve<3>(v, ys); break;
+        }
+    }
+    // the neighbours' summaries have landed (bounded wait)
+    const bool got = mbar_wait(rbar, 0u, status);
+    if (col) {
+        const float h = (has_up && got) ? rh[c] : 0.0f;
+        const float b = (has_dn && got) ? rb[c] : 0.0f;
+        switch (kind) {
+            case 0: tile_halo_add<0>(v, ys, h, b); break;
+            case 1: tile_halo_add<1>(v, ys, h, b); break;
+            case 2: tile_halo_add<2>(v, ys, h, b); break;
+            default: break;
+        }
+    }
     if (col && TRID_BOUNDS(in_span(int64_t(z) * plane + int64_t(y0) * nx + c,
                                    int64_t(WA_YT - 1) * nx + 1, total))) {
         float *ecol = e + size_t(z) * size_t(plane) + size_t(y0) * nx + c;
 #pragma unroll
-        for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[WIN_H + j] + sz[j * nx + cs];
+        for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[j] + sz[j * nx + cs];
     }
-    // no CTA leaves while a neighbour may still read its shared memory
+    // no CTA leaves while a summary it sent may still be in flight
+    cluster_arrive_relaxed();
     cluster_wait_acquire();
 }
 
@@ -518,6 +607,66 @@ inline double win_fill(WinTab<T, W> &tab, int n, int tile_rows, double lam) {
             tab.C[k][j] = T(C[j]);
         }
         if (occurs[k]) worst = fmax(worst, tr);
+    }
+    return worst;
+}
+
+// Tables of the split y window solve (see WinSplit) for a line of n nodes in
+// 32-row tiles, from the window factors in double; returns the largest
+// truncation factor over the kinds that occur (as win_fill).
+inline double winsplit_fill(WinSplit &ys, int n, double lam) {
+    constexpr int W = WA_W, H = WIN_H, Y = WA_YT;
+    const int ntile = n / Y;
+    const int rep[4] = {0, ntile >= 3 ? 1 : 0, ntile - 1, 0};
+    const bool occurs[4] = {ntile >= 2, ntile >= 3, ntile >= 2, ntile == 1};
+    double worst = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double F[W], FA[W], C[W], tr = 0.0;
+        win_fill_one<W>(F, FA, C, n, rep[k], Y, lam, tr);
+        if (occurs[k]) worst = fmax(worst, tr);
+        const bool top = rep[k] > 0, bot = (rep[k] + 1) * Y < n;
+        for (int j = 0; j < Y; ++j) {
+            ys.F[k][j] = float(F[H + j]);
+            ys.FA[k][j] = float(FA[H + j]);
+            ys.C[k][j] = float(C[H + j]);
+        }
+        // x_40 per unit f_39 with the halo below zero
+        double f[W], x[W];
+        f[H + Y - 1] = 1.0;
+        for (int j = H + Y; j < W; ++j) f[j] = FA[j] * f[j - 1];
+        double xv = f[W - 1];
+        for (int j = W - 2; j >= H + Y; --j) xv = f[j] - C[j] * xv;
+        ys.R[k] = float(bot ? xv : 0.0);
+        // response of the tile rows to a unit forward value at row 7
+        f[H - 1] = 1.0;
+        for (int j = H; j < W; ++j) f[j] = FA[j] * f[j - 1];
+        x[W - 1] = f[W - 1];
+        for (int j = W - 2; j >= H; --j) x[j] = f[j] - C[j] * x[j + 1];
+        for (int j = 0; j < Y; ++j) ys.T[k][j] = float(top ? x[H + j] : 0.0);
+        // response of the tile rows to a unit x_40
+        xv = 1.0;
+        for (int j = H + Y - 1; j >= H; --j) {
+            xv = -C[j] * xv;
+            ys.B[k][j - H] = float(bot ? xv : 0.0);
+        }
+        // h per value of each row above: F_k prod_{i > k} FA_i up to row 7
+        for (int m = 0; m < H; ++m) {
+            double w = F[m];
+            for (int i = m + 1; i < H; ++i) w *= FA[i];
+            ys.Wt[k][m] = float(top ? w : 0.0);
+        }
+        // b per value of each row below: the window solve of rows 40..47 alone
+        for (int m = 0; m < H; ++m) {
+            double g[W];
+            for (int j = 0; j < W; ++j) g[j] = 0.0;
+            for (int j = H + Y; j < W; ++j) {
+                const double vj = (j == H + Y + m) ? 1.0 : 0.0;
+                g[j] = F[j] * vj + FA[j] * g[j - 1];
+            }
+            double xb = g[W - 1];
+            for (int j = W - 2; j >= H + Y; --j) xb = g[j] - C[j] * xb;
+            ys.Wb[k][m] = float(bot ? xb : 0.0);
+        }
     }
     return worst;
 }
