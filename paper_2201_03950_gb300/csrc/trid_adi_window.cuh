@@ -277,9 +277,16 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     cluster_arrive_relaxed();
     pdl_trigger();
     pdl_wait();  // u is written by the previous kernel on the stream
-    // the z neighbours of every row of the group, all in flight at once:
-    // plane z - 1 lands where X^{-1} d of the row will go, plane z + 1 where
-    // its Z u will go (each lane copies, and later reads, only its own chunks)
+    // the rows y - 1 .. y + 1 of the group's first row first, then the z
+    // neighbours of every row of the group (all in flight at once; plane
+    // z - 1 lands where X^{-1} d of the row will go, plane z + 1 where its
+    // Z u will go, each lane copying, and later reading, only its own chunks),
+    // then the row y + 2
+    const bool yok0 = y0 + r0 - 1 >= 0;
+    float ym[M], uc[M], yp[M], yq[M];  // rows y - 1 .. y + 2 of the group's first row
+    ld(r0 - 1, 0, gact && yok0, ym);
+    ld(r0, 0, gact, uc);
+    ld(r0 + 1, 0, gact && y0 + r0 + 1 < ny, yp);
 #pragma unroll
     for (int i = 0; i < RG; ++i) {
         const int r = r0 + i;
@@ -295,11 +302,6 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
         }
         cp_async_commit();
     }
-    const bool yok0 = y0 + r0 - 1 >= 0;
-    float ym[M], uc[M], yp[M], yq[M];  // rows y - 1 .. y + 2 of the group's first row
-    ld(r0 - 1, 0, gact && yok0, ym);
-    ld(r0, 0, gact, uc);
-    ld(r0 + 1, 0, gact && y0 + r0 + 1 < ny, yp);
     ld(r0 + 2, 0, gact && RG > 1 && y0 + r0 + 2 < ny, yq);
     const int rt = sx.real_tiles;
     const bool firstx = (g == 0), lastx = (g == rt - 1);
