@@ -288,17 +288,23 @@ trid_status trid_get_device_status(trid_stream_t stream);
 trid_status trid_wait_flag(const int *flag, int expect, double timeout_s, trid_stream_t stream);
 
 /*
- * Length classes of trid_solve_batch_varlen: systems of up to 248 rows are
- * solved by one warp each, up to team_max rows by a team of 4 warps, up to
- * block_max rows by a whole block in one pass, and longer ones by a block in
- * two passes.  team_max is 248 (no team class), 504 or 1016; block_max is
- * team_max (no one-pass block class) or one of 1016, 2040, 4088 not below
- * team_max.  Defaults (trid_solve_batch_varlen): team_max 1016, block_max
- * 4088.  Not a construct of the paper (its FPGA batches are uniform).
+ * Length classes and tile height of trid_solve_batch_varlen.  Every thread
+ * holds tiles of tile_rows consecutive rows (M = 8, or 16 in FP32; 0 means 8).
+ * Systems of up to 32 M - M rows are solved by one warp each, up to team_max
+ * rows by a team of 4 warps, up to block_max rows by a whole block (512
+ * threads) in one pass, and longer ones by a block in two passes.  With M = 8:
+ * team_max is 248 (no team class), 504 or 1016; block_max is team_max (no
+ * one-pass block class) or one of 1016, 2040, 4088 not below team_max.  With
+ * M = 16 every limit doubles plus 8 (team_max 496, 1008 or 2032; block_max
+ * team_max or one of 2032, 4080, 8176).  Defaults (trid_solve_batch_varlen):
+ * M 8, team_max 1016, block_max 4088.  A caller zero-initialises the struct
+ * and sets the fields it uses.  Not a construct of the paper (its FPGA
+ * batches are uniform).
  */
 typedef struct {
     int32_t team_max;
     int32_t block_max;
+    int32_t tile_rows;
 } trid_varlen_config;
 
 /* trid_solve_batch_varlen with explicit length classes (cfg == NULL: the
@@ -309,7 +315,8 @@ trid_status trid_solve_batch_varlen_cfg(const void *a, const void *b, const void
                                         void *workspace, size_t workspace_bytes,
                                         trid_stream_t stream, const trid_varlen_config *cfg);
 
-/* Autotuner: solves the caller's batch once per admissible configuration (on
+/* Autotuner: solves the caller's batch once per admissible configuration
+ * (every tile height and class split above; tile height 16 in FP32 only) (on
  * a scratch copy of d inside `workspace`; a, b, c, d are not modified), times
  * each with CUDA events on `stream` (best of three after one warm-up run) and
  * writes the fastest to *best (and its time in ms to *best_ms if not NULL).

@@ -11,10 +11,11 @@
 //                   below forced onto bucket edges) and k_varlen_scatter
 //                   (meta[]: first row and length, longest bucket first).
 //   k_varlen_solve  persistent; every block takes the classes in turn, each
-//                   from its own atomic counter, longest first:
+//                   from its own atomic counter, longest first (row limits
+//                   for tiles of M = 8 rows; tile_rows 16 doubles them):
 //     L   (> 4088 rows)  one system per block, two passes: pass 1 reads the
 //                        system and writes the two reduced rows of every
-//                        8-row tile to shared memory; the reduced system is
+//                        M-row tile to shared memory; the reduced system is
 //                        reduced again in shared memory until one warp can
 //                        solve it, and substituted back level by level; pass 2
 //                        re-reads the system (L2-resident), repeats the tile
@@ -35,25 +36,27 @@
 
 namespace trid {
 
-constexpr int VL_M = 8;               // tile height
-constexpr int VL_SHORT = 32 * VL_M;   // most rows (with alignment padding) one warp solves
-constexpr int VL_SHORT_N = VL_SHORT - VL_M;  // systems up to this length go to one warp
+// Tile height M (rows per thread) is a template parameter: 8 (any dtype) or
+// 16 (FP32).  The class limits follow from it.
 constexpr int VL_THREADS = 512;       // threads per block of the persistent kernel
 constexpr int VL_TEAM = 128;          // threads of an M1 team
-constexpr int VL_M1_N = VL_TEAM * VL_M - VL_M;      // 1016: longest M1 system
-constexpr int VL_M2_N = VL_THREADS * VL_M - VL_M;   // 4088: longest M2 system
 constexpr int VL_BUCKETS = 40;
 constexpr int VL_PLAN_THREADS = 256;
+__host__ __device__ constexpr int vl_log2(int m) { return m == 16 ? 4 : 3; }
+__host__ __device__ constexpr int vl_short_n(int m) { return 32 * m - m; }   // one warp
+__host__ __device__ constexpr int vl_m1_n(int m) { return VL_TEAM * m - m; }  // one team
+__host__ __device__ constexpr int vl_m2_n(int m) { return VL_THREADS * m - m; }  // one block
 // Buckets are ceil log2 of the length, raised to the class edges for lengths
 // above the smaller class's limit.  The first M1 bucket is fixed; the first M2
 // and L buckets (e1, e2) are run-time choices (trid_varlen_config, picked by
 // trid_varlen_autotune): a class spanning buckets [lo, hi) holds lengths up to
-// 2^(hi-1) - 8, the padding of a 16-byte-aligned tile start included.
-constexpr int VL_B_M1 = 9;
-constexpr int VL_E1_DEFAULT = 11, VL_E2_DEFAULT = 13;  // M1 <= 1016, M2 <= 4088
+// 2^(hi-1) - M, the padding of a 16-byte-aligned tile start included.
+__host__ __device__ constexpr int vl_b_m1(int m) { return 6 + vl_log2(m); }
+__host__ __device__ constexpr int vl_e1_default(int m) { return 8 + vl_log2(m); }  // M1 <= 128 M - M
+__host__ __device__ constexpr int vl_e2_default(int m) { return 10 + vl_log2(m); }  // M2 <= 512 M - M
 
-__host__ __device__ __forceinline__ int64_t vl_class_max(int edge) {
-    return (int64_t(1) << (edge - 1)) - VL_M;
+__host__ __device__ __forceinline__ int64_t vl_class_max(int edge, int m) {
+    return (int64_t(1) << (edge - 1)) - m;
 }
 
 struct VarlenWork {
@@ -72,14 +75,14 @@ inline size_t varlen_ws_bytes(int64_t nsys) {
 }
 
 // ceil(log2 n) (0 for n <= 1), raised so that each class occupies whole
-// buckets: S <= 8, M1 9..10, M2 11..12, L >= 13 (every length fits its class:
-// 2^8 = 256 > 248, 2^10 = 1024 > 1016, 2^12 = 4096 > 4088).
-__device__ __forceinline__ int len_bucket(int64_t n, int e1, int e2) {
+// buckets (for M = 8: S <= 8, M1 9..10, M2 11..12, L >= 13; every length fits
+// its class: 2^8 = 256 > 248, 2^10 = 1024 > 1016, 2^12 = 4096 > 4088).
+__device__ __forceinline__ int len_bucket(int64_t n, int e1, int e2, int m) {
     if (n <= 1) return 0;
     int b = 64 - __clzll((unsigned long long)(n - 1));
-    if (n > VL_SHORT_N && b < VL_B_M1) b = VL_B_M1;
-    if (e1 > VL_B_M1 && n > vl_class_max(e1) && b < e1) b = e1;
-    if (n > vl_class_max(e2) && b < e2) b = e2;
+    if (n > vl_short_n(m) && b < vl_b_m1(m)) b = vl_b_m1(m);
+    if (e1 > vl_b_m1(m) && n > vl_class_max(e1, m) && b < e1) b = e1;
+    if (n > vl_class_max(e2, m) && b < e2) b = e2;
     return b < VL_BUCKETS ? b : VL_BUCKETS - 1;
 }
 
@@ -118,21 +121,21 @@ __device__ __forceinline__ int64_t plan_len(const int64_t *__restrict__ offsets,
 
 __global__ void __launch_bounds__(VL_PLAN_THREADS)
 k_varlen_hist(const int64_t *__restrict__ offsets, int64_t nsys, int64_t total, VarlenWork *work,
-              int *status, int e1, int e2) {
+              int *status, int e1, int e2, int m) {
     __shared__ unsigned long long hist[VL_BUCKETS];
     const int tid = threadIdx.x;
     if (tid < VL_BUCKETS) hist[tid] = 0;
     __syncthreads();
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + tid; k < nsys;
          k += int64_t(gridDim.x) * blockDim.x)
-        atomicAdd(&hist[len_bucket(plan_len(offsets, k, total, status, true), e1, e2)], 1ull);
+        atomicAdd(&hist[len_bucket(plan_len(offsets, k, total, status, true), e1, e2, m)], 1ull);
     __syncthreads();
     if (tid < VL_BUCKETS && hist[tid]) atomicAdd(&work->hist[tid], hist[tid]);
 }
 
 __global__ void __launch_bounds__(VL_PLAN_THREADS)
 k_varlen_scatter(const int64_t *__restrict__ offsets, int64_t nsys, int64_t total,
-                 VarlenWork *work, longlong2 *__restrict__ meta, int e1, int e2) {
+                 VarlenWork *work, longlong2 *__restrict__ meta, int e1, int e2, int m) {
     __shared__ unsigned long long hist[VL_BUCKETS];
     __shared__ unsigned long long start[VL_BUCKETS];
     const int tid = threadIdx.x;
@@ -144,7 +147,7 @@ k_varlen_scatter(const int64_t *__restrict__ offsets, int64_t nsys, int64_t tota
         int b = -1;
         unsigned long long local = 0;
         if (k < nsys) {
-            b = len_bucket(plan_len(offsets, k, total, nullptr, false), e1, e2);
+            b = len_bucket(plan_len(offsets, k, total, nullptr, false), e1, e2, m);
             local = atomicAdd(&hist[b], 1ull);
         }
         __syncthreads();
@@ -170,8 +173,8 @@ struct RLevel {
     int R;
 };
 
-// Tile pass of level `src` (tiles of 8 rows) into the reduced rows of `dst`.
-template <typename T>
+// Tile pass of level `src` (tiles of M rows) into the reduced rows of `dst`.
+template <typename T, int VL_M>
 __device__ void level_reduce(const RLevel<T> &src, RLevel<T> &dst) {
     const int nt = (src.R + VL_M - 1) / VL_M;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
@@ -194,7 +197,7 @@ __device__ void level_reduce(const RLevel<T> &src, RLevel<T> &dst) {
 
 // Substitute the solution of `dst` (held in dst.d) back into level `src`,
 // writing src's solution into src.d.
-template <typename T>
+template <typename T, int VL_M>
 __device__ void level_substitute(RLevel<T> &src, const RLevel<T> &dst) {
     const int nt = (src.R + VL_M - 1) / VL_M;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
@@ -217,8 +220,8 @@ __device__ void level_substitute(RLevel<T> &src, const RLevel<T> &dst) {
     }
 }
 
-// One warp solves a level of R <= 256 rows in place (lane tiles, shuffles).
-template <typename T>
+// One warp solves a level of R <= 32 M rows in place (lane tiles, shuffles).
+template <typename T, int VL_M>
 __device__ void level_warp_solve(RLevel<T> &lv) {
     const int lane = threadIdx.x & 31;
     T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
@@ -244,13 +247,13 @@ __device__ void level_warp_solve(RLevel<T> &lv) {
 // s0 is read as if it began `pad` = s0 mod (16 / sizeof(T)) identity rows
 // earlier (a = c = d = 0, b = 1: decoupled, x = 0), so every tile starts on a
 // 16-byte boundary and is loaded with vector loads when it lies inside the
-// arrays.  Row j of tile t is system row 8t + j - pad.
+// arrays.  Row j of tile t is system row M t + j - pad.
 template <typename T>
 __device__ __forceinline__ int sys_pad(int64_t s0) {
     return int(s0 % (16 / int(sizeof(T))));
 }
 
-template <typename T>
+template <typename T, int VL_M>
 __device__ __forceinline__ void load_sys_tile(const T *__restrict__ a, const T *__restrict__ b,
                                               const T *__restrict__ c, const T *d, int64_t s0,
                                               int64_t n, int pad, int64_t total, int64_t t,
@@ -282,7 +285,7 @@ __device__ __forceinline__ void load_sys_tile(const T *__restrict__ a, const T *
     }
 }
 
-template <typename T>
+template <typename T, int VL_M>
 __device__ __forceinline__ void store_sys_tile(T *out, int accumulate, int64_t s0, int64_t n,
                                                int pad, int64_t total, int64_t t,
                                                const T (&rd)[VL_M]) {
@@ -350,19 +353,19 @@ __device__ void block_pcr(RLevel<T> &lv) {
 // synchronised): tile passes in shared memory while it is longer than two rows
 // per thread, the block PCR on the top level, then substitution back down to
 // level 0 (whose solution is then in lv[0].d).  All threads of the block call it.
-template <typename T>
+template <typename T, int VL_M>
 __device__ void block_reduced_solve(RLevel<T> *lv, int nlevels) {
     int top = 0;
     while (lv[top].R > 2 * int(blockDim.x) && top + 1 < nlevels) {
         lv[top + 1].R = 2 * ((lv[top].R + VL_M - 1) / VL_M);
-        level_reduce<T>(lv[top], lv[top + 1]);
+        level_reduce<T, VL_M>(lv[top], lv[top + 1]);
         __syncthreads();
         ++top;
     }
     block_pcr<T>(lv[top]);
     __syncthreads();
     for (int l = top - 1; l >= 0; --l) {
-        level_substitute<T>(lv[l], lv[l + 1]);
+        level_substitute<T, VL_M>(lv[l], lv[l + 1]);
         __syncthreads();
     }
 }
@@ -390,13 +393,14 @@ __device__ __forceinline__ VItem vitem_fetch(unsigned long long *ctr, int64_t li
     return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(VL_THREADS, sizeof(T) == 4 ? 2 : 1)
+template <typename T, int VL_M>
+__global__ void __launch_bounds__(VL_THREADS, (sizeof(T) == 4 && VL_M == 8) ? 2 : 1)
 k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c, const T *d,
                T *out, int accumulate, int64_t nsys, int64_t total, int64_t max_len,
                VarlenWork *work, const longlong2 *__restrict__ meta, int nlevels, int *status,
                int e1, int e2) {
-    const int64_t m1_max = vl_class_max(e1), m2_max = vl_class_max(e2);
+    constexpr int VL_M2_N = vl_m2_n(VL_M), VL_SHORT_N = vl_short_n(VL_M);
+    const int64_t m1_max = vl_class_max(e1, VL_M), m2_max = vl_class_max(e2, VL_M);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ VItem s_it[2];
     __shared__ VItem s_team_it[VL_THREADS / VL_TEAM][2];
@@ -417,7 +421,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
     const int helper = blockDim.x - 1;
     const int64_t n_l = int64_t(n_in_buckets(work, e2, VL_BUCKETS));
     const int64_t n_m2 = int64_t(n_in_buckets(work, e1, e2));
-    const int64_t n_m1 = int64_t(n_in_buckets(work, VL_B_M1, e1));
+    const int64_t n_m1 = int64_t(n_in_buckets(work, vl_b_m1(VL_M), e1));
     const int64_t n_s = nsys - n_l - n_m2 - n_m1;
 
     // ---- class L: one system per block, two passes
@@ -437,7 +441,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         lv[0].R = int(2 * ntiles);
         for (int64_t t = tid; t < ntiles; t += blockDim.x) {
             T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
-            load_sys_tile<T>(a, b, c, d, s0, n, pad, total, t, ra, rb, rc, rd);
+            load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, t, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
             lv[0].a[2 * t] = as; lv[0].c[2 * t] = cs; lv[0].d[2 * t] = ds;
@@ -446,16 +450,16 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         longlong2 nx_meta = make_longlong2(0, 0);
         if (tid == helper && (long long)nx_item < n_l) nx_meta = meta[nx_item];
         __syncthreads();
-        if (ok) block_reduced_solve<T>(lv, nlevels);
+        if (ok) block_reduced_solve<T, VL_M>(lv, nlevels);
         if (tid == helper) s_it[cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
         // pass 2: recompute every tile and substitute its end values
         for (int64_t t = tid; t < ntiles; t += blockDim.x) {
             T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
-            load_sys_tile<T>(a, b, c, d, s0, n, pad, total, t, ra, rb, rc, rd);
+            load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, t, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
             tile_substitute<T, VL_M>(ra, rc, rd, lv[0].d[2 * t], lv[0].d[2 * t + 1]);
-            store_sys_tile<T>(out, accumulate, s0, n, pad, total, t, rd);
+            store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, t, rd);
         }
         __syncthreads();  // level 0 is rewritten by the next system
     }
@@ -477,7 +481,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
         lv[0].R = 2 * ntiles;
         if (mine) {
-            load_sys_tile<T>(a, b, c, d, s0, n, pad, total, tid, ra, rb, rc, rd);
+            load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, tid, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
             lv[0].a[2 * tid] = as; lv[0].c[2 * tid] = cs; lv[0].d[2 * tid] = ds;
@@ -486,11 +490,11 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         longlong2 nx_meta = make_longlong2(0, 0);
         if (tid == helper && (long long)nx_item < n_m2) nx_meta = meta[n_l + nx_item];
         __syncthreads();
-        if (ok) block_reduced_solve<T>(lv, nlevels);
+        if (ok) block_reduced_solve<T, VL_M>(lv, nlevels);
         if (tid == helper) s_it[cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
         if (mine) {
             tile_substitute<T, VL_M>(ra, rc, rd, lv[0].d[2 * tid], lv[0].d[2 * tid + 1]);
-            store_sys_tile<T>(out, accumulate, s0, n, pad, total, tid, rd);
+            store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, tid, rd);
         }
         __syncthreads();
     }
@@ -521,7 +525,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
             tl.R = 2 * ntiles;
             if (mine) {
-                load_sys_tile<T>(a, b, c, d, s0, n, pad, total, tt, ra, rb, rc, rd);
+                load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, tt, ra, rb, rc, rd);
                 T as, cs, ds, ae, ce, de;
                 tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
                 tl.a[2 * tt] = as; tl.c[2 * tt] = cs; tl.d[2 * tt] = ds;
@@ -530,13 +534,13 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             longlong2 nx_meta = make_longlong2(0, 0);
             if (tt == thelper && (long long)nx_item < n_m1) nx_meta = meta[base1 + nx_item];
             named_barrier_sync(bar, VL_TEAM);
-            if (ok && tt < 32) level_warp_solve<T>(tl);
+            if (ok && tt < 32) level_warp_solve<T, VL_M>(tl);
             if (tt == thelper)
                 s_team_it[team][cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
             named_barrier_sync(bar, VL_TEAM);
             if (mine) {
                 tile_substitute<T, VL_M>(ra, rc, rd, tl.d[2 * tt], tl.d[2 * tt + 1]);
-                store_sys_tile<T>(out, accumulate, s0, n, pad, total, tt, rd);
+                store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, tt, rd);
             }
             named_barrier_sync(bar, VL_TEAM);  // the team's rows are rewritten next
         }
@@ -557,7 +561,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             const bool ok = n > 0 && n <= VL_SHORT_N && sys_valid(s0, n, total);
             const int pad = sys_pad<T>(s0);
             T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
-            if (ok) load_sys_tile<T>(a, b, c, d, s0, n, pad, total, lane, ra, rb, rc, rd);
+            if (ok) load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, lane, ra, rb, rc, rd);
             if (lane == 31) {
                 it.item = (long long)nx_item;
                 it.s0 = 0;
@@ -573,14 +577,15 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
             group_solve<T, 32>(as, cs, ds, ae, ce, de, lane, xs, xe);
             tile_substitute<T, VL_M>(ra, rc, rd, xs, xe);
-            store_sys_tile<T>(out, accumulate, s0, n, pad, total, lane, rd);
+            store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, lane, rd);
         }
     }
 }
 
 // Levels and shared-memory bytes for systems up to max_len rows.
-template <typename T>
+template <typename T, int VL_M>
 static bool varlen_levels(int64_t max_len, int &nlevels, size_t &smem) {
+    constexpr int VL_M2_N = vl_m2_n(VL_M), VL_SHORT = 32 * VL_M;
     if (max_len < VL_M2_N) max_len = VL_M2_N;  // the M2 class uses the same levels
     int64_t R = 2 * ((max_len + 2 * VL_M - 1) / VL_M);
     nlevels = 0;
@@ -598,13 +603,13 @@ static bool varlen_levels(int64_t max_len, int &nlevels, size_t &smem) {
     return true;
 }
 
-template <typename T>
+template <typename T, int VL_M>
 static trid_status varlen_run(const T *a, const T *b, const T *c, const T *d, T *out, int acc,
                               const int64_t *offsets, int64_t nsys, int64_t total, int64_t max_len,
                               void *ws, cudaStream_t st, int e1, int e2) {
     int nlevels = 0;
     size_t smem = 0;
-    if (!varlen_levels<T>(max_len, nlevels, smem)) return TRID_ERR_UNSUPPORTED;
+    if (!varlen_levels<T, VL_M>(max_len, nlevels, smem)) return TRID_ERR_UNSUPPORTED;
     const DeviceInfo *di = device_info();
     if (!di) return TRID_ERR_CUDA;
     if (smem > size_t(di->max_smem_optin) - 512) return TRID_ERR_UNSUPPORTED;
@@ -615,11 +620,12 @@ static trid_status varlen_run(const T *a, const T *b, const T *c, const T *d, T 
     if (pblocks > 4 * int64_t(di->sm_count)) pblocks = 4 * int64_t(di->sm_count);
     if (cudaMemsetAsync(work, 0, sizeof(VarlenWork), st) != cudaSuccess) return TRID_ERR_CUDA;
     k_varlen_hist<<<dim3(unsigned(pblocks)), VL_PLAN_THREADS, 0, st>>>(offsets, nsys, total, work,
-                                                                      device_status_word(), e1, e2);
+                                                                      device_status_word(), e1, e2,
+                                                                      VL_M);
     k_varlen_scatter<<<dim3(unsigned(pblocks)), VL_PLAN_THREADS, 0, st>>>(offsets, nsys, total,
-                                                                         work, meta, e1, e2);
+                                                                         work, meta, e1, e2, VL_M);
     if (cudaGetLastError() != cudaSuccess) return TRID_ERR_CUDA;
-    auto kern = k_varlen_solve<T>;
+    auto kern = k_varlen_solve<T, VL_M>;
     const int per_sm = kernel_blocks_per_sm(reinterpret_cast<const void *>(kern), VL_THREADS, smem);
     if (per_sm < 1) return TRID_ERR_UNSUPPORTED;
     int64_t grid = int64_t(di->sm_count) * per_sm;
@@ -638,18 +644,25 @@ extern "C" size_t trid_solve_varlen_workspace_bytes(int64_t nsys) {
     return varlen_ws_bytes(nsys);
 }
 
-// Class edges of a configuration (see trid_varlen_config in include/trid.h).
-static bool vl_edges(const trid_varlen_config *cfg, int &e1, int &e2) {
-    if (!cfg) { e1 = VL_E1_DEFAULT; e2 = VL_E2_DEFAULT; return true; }
-    auto edge_of = [](int32_t len, int &e) {
-        for (int k = VL_B_M1; k <= VL_E2_DEFAULT; ++k)
-            if (vl_class_max(k) == len) { e = k; return true; }
+// Tile height and class edges of a configuration (see trid_varlen_config in
+// include/trid.h); false for a configuration outside the admissible list.
+static bool vl_edges(const trid_varlen_config *cfg, trid_dtype dtype, int &m, int &e1, int &e2) {
+    m = 8;
+    if (cfg && cfg->tile_rows != 0 && cfg->tile_rows != 8) {
+        if (cfg->tile_rows != 16 || dtype != TRID_F32) return false;
+        m = 16;
+    }
+    if (!cfg) { e1 = vl_e1_default(m); e2 = vl_e2_default(m); return true; }
+    const int lo = vl_b_m1(m), e1max = vl_e1_default(m), e2max = vl_e2_default(m);
+    auto edge_of = [&](int32_t len, int &e) {
+        for (int k = lo; k <= e2max; ++k)
+            if (vl_class_max(k, m) == len) { e = k; return true; }
         return false;
     };
-    if (cfg->team_max == VL_SHORT_N) e1 = VL_B_M1;
-    else if (!edge_of(cfg->team_max, e1) || e1 > VL_E1_DEFAULT) return false;
+    if (cfg->team_max == vl_short_n(m)) e1 = lo;
+    else if (!edge_of(cfg->team_max, e1) || e1 > e1max) return false;
     if (cfg->block_max == cfg->team_max) e2 = e1;
-    else if (!edge_of(cfg->block_max, e2) || e2 > VL_E2_DEFAULT || e2 < e1) return false;
+    else if (!edge_of(cfg->block_max, e2) || e2 > e2max || e2 < e1) return false;
     return true;
 }
 
@@ -660,8 +673,8 @@ static trid_status varlen_entry(const void *a, const void *b, const void *c, voi
                                 const trid_varlen_config *cfg) {
     if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
     if (nsys < 0 || total < 0 || max_len < 0) return TRID_ERR_INVALID_ARG;
-    int e1, e2;
-    if (!vl_edges(cfg, e1, e2)) return TRID_ERR_INVALID_ARG;
+    int m, e1, e2;
+    if (!vl_edges(cfg, dtype, m, e1, e2)) return TRID_ERR_INVALID_ARG;
     if (nsys == 0 || total == 0) return TRID_OK;
     if (!a || !b || !c || !d || !offsets) return TRID_ERR_INVALID_ARG;
     const size_t esz = dtype == TRID_F32 ? 4 : 8;
@@ -683,12 +696,17 @@ static trid_status varlen_entry(const void *a, const void *b, const void *c, voi
     if (max_len == 0) max_len = 1;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int acc = u ? 1 : 0;
-    if (dtype == TRID_F32)
-        return varlen_run<float>(static_cast<const float *>(a), static_cast<const float *>(b),
-                                 static_cast<const float *>(c), static_cast<const float *>(d),
-                                 static_cast<float *>(u ? u : d), acc, offsets, nsys, total,
-                                 max_len, workspace, st, e1, e2);
-    return varlen_run<double>(static_cast<const double *>(a), static_cast<const double *>(b),
+    if (dtype == TRID_F32) {
+        const float *fa = static_cast<const float *>(a), *fb = static_cast<const float *>(b);
+        const float *fc = static_cast<const float *>(c), *fd = static_cast<const float *>(d);
+        float *fo = static_cast<float *>(u ? u : d);
+        if (m == 16)
+            return varlen_run<float, 16>(fa, fb, fc, fd, fo, acc, offsets, nsys, total, max_len,
+                                         workspace, st, e1, e2);
+        return varlen_run<float, 8>(fa, fb, fc, fd, fo, acc, offsets, nsys, total, max_len,
+                                    workspace, st, e1, e2);
+    }
+    return varlen_run<double, 8>(static_cast<const double *>(a), static_cast<const double *>(b),
                               static_cast<const double *>(c), static_cast<const double *>(d),
                               static_cast<double *>(u ? u : d), acc, offsets, nsys, total,
                               max_len, workspace, st, e1, e2);
@@ -732,8 +750,9 @@ extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const 
                                             float *best_ms) {
     trid::NvtxScope nvtx_scope("trid_varlen_autotune");
     if (!best) return TRID_ERR_INVALID_ARG;
-    best->team_max = int32_t(vl_class_max(VL_E1_DEFAULT));
-    best->block_max = int32_t(vl_class_max(VL_E2_DEFAULT));
+    best->team_max = int32_t(vl_class_max(vl_e1_default(8), 8));
+    best->block_max = int32_t(vl_class_max(vl_e2_default(8), 8));
+    best->tile_rows = 8;
     if (best_ms) *best_ms = 0.0f;
     if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
     if (nsys < 0 || total < 0 || max_len < 0) return TRID_ERR_INVALID_ARG;
@@ -746,9 +765,6 @@ extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const 
     const size_t wsb = (varlen_ws_bytes(nsys) + 255) / 256 * 256;
     void *scratch = static_cast<char *>(workspace) + wsb;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int32_t teams[3] = {VL_SHORT_N, int32_t(vl_class_max(10)), int32_t(vl_class_max(11))};
-    const int32_t blocks[4] = {int32_t(vl_class_max(11)), int32_t(vl_class_max(12)),
-                               int32_t(vl_class_max(13)), 0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
@@ -757,12 +773,20 @@ extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const 
     }
     float best_t = -1.0f;
     trid_status rs = TRID_OK;
+    const int nm = dtype == TRID_F32 ? 2 : 1;  // tile heights 8 (and 16 in FP32)
+    for (int mi = 0; mi < nm && rs == TRID_OK; ++mi) {
+    const int m = mi == 0 ? 8 : 16;
+    const int32_t teams[3] = {vl_short_n(m), int32_t(vl_class_max(vl_b_m1(m) + 1, m)),
+                              int32_t(vl_class_max(vl_b_m1(m) + 2, m))};
+    const int32_t blocks[4] = {int32_t(vl_class_max(vl_b_m1(m) + 2, m)),
+                               int32_t(vl_class_max(vl_b_m1(m) + 3, m)),
+                               int32_t(vl_class_max(vl_b_m1(m) + 4, m)), 0};
     for (int ti = 0; ti < 3 && rs == TRID_OK; ++ti) {
         for (int bi = 0; bi < 4 && rs == TRID_OK; ++bi) {
             if (bi < 3 && blocks[bi] == teams[ti]) continue;  // same as bi == 3
-            trid_varlen_config cfg{teams[ti], bi == 3 ? teams[ti] : blocks[bi]};
-            int ea, eb;
-            if (!vl_edges(&cfg, ea, eb)) continue;
+            trid_varlen_config cfg{teams[ti], bi == 3 ? teams[ti] : blocks[bi], m};
+            int mm, ea, eb;
+            if (!vl_edges(&cfg, dtype, mm, ea, eb)) continue;
             float t_best = -1.0f;
             for (int rep = 0; rep < 4 && rs == TRID_OK; ++rep) {  // first run warms up
                 if (cudaMemcpyAsync(scratch, d, size_t(total) * esz, cudaMemcpyDeviceToDevice,
@@ -782,6 +806,7 @@ extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const 
                 *best = cfg;
             }
         }
+    }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -197,11 +197,14 @@ def varlen_workspace_bytes(nsys: int) -> int:
 
 
 class VarlenConfig(ctypes.Structure):
-    """Length classes of the uneven-batch solver (trid_varlen_config)."""
-    _fields_ = [("team_max", ctypes.c_int32), ("block_max", ctypes.c_int32)]
+    """Length classes and tile height of the uneven-batch solver
+    (trid_varlen_config; tile_rows 0 means 8)."""
+    _fields_ = [("team_max", ctypes.c_int32), ("block_max", ctypes.c_int32),
+                ("tile_rows", ctypes.c_int32)]
 
     def __repr__(self):
-        return f"VarlenConfig(team_max={self.team_max}, block_max={self.block_max})"
+        return (f"VarlenConfig(team_max={self.team_max}, block_max={self.block_max}, "
+                f"tile_rows={self.tile_rows or 8})")
 
 
 def _check_offsets(offsets):
@@ -214,7 +217,8 @@ def solve_varlen(a, b, c, d, offsets, max_len: int, u=None, workspace=None, stre
                  config: VarlenConfig | None = None):
     """Batch of systems of different lengths: system k occupies rows
     [offsets[k], offsets[k+1]) (offsets: int64 CUDA tensor of nsys + 1).
-    ``config``: length classes (e.g. from ``varlen_autotune``); None = defaults."""
+    ``config``: length classes and tile height (e.g. from ``varlen_autotune``);
+    None = defaults."""
     import torch
     total = d.numel()
     _check_tensors((a, b, c, d, u), d, total)
@@ -257,7 +261,7 @@ def _tune_cache_path():
 
 
 def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None, cache: bool = True):
-    """Time every admissible length-class configuration on this batch (d is
+    """Time every admissible configuration (tile height, length classes) on this batch (d is
     not modified) and return (best VarlenConfig, its time in ms).  With
     ``cache`` the choice is kept in a JSON file (TRID_TUNE_CACHE, else
     ~/.cache/gb300-trid/varlen_tune.json) keyed by dtype and length histogram;
@@ -280,7 +284,8 @@ def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None, cache: bool 
             table = {}
         hit = table.get(key)
         if hit is not None:
-            return VarlenConfig(int(hit["team_max"]), int(hit["block_max"])), -1.0
+            return VarlenConfig(int(hit["team_max"]), int(hit["block_max"]),
+                                int(hit.get("tile_rows", 8))), -1.0
     L = load()
     ws = torch.empty(max(int(L.trid_varlen_autotune_workspace_bytes(nsys, total, _dtype(d))), 1),
                      dtype=torch.uint8, device=d.device)
@@ -294,7 +299,7 @@ def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None, cache: bool 
         raise TridError(st, "trid_varlen_autotune")
     if cache:
         table[key] = {"team_max": int(best.team_max), "block_max": int(best.block_max),
-                      "ms": float(ms.value)}
+                      "tile_rows": int(best.tile_rows or 8), "ms": float(ms.value)}
         path = _tune_cache_path()
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)

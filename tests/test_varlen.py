@@ -158,9 +158,14 @@ CLASS_EDGES = [248, 249, 503, 504, 505, 1015, 1016, 1017, 2039, 2040, 2041, 4087
                5000, 1, 2, 200]
 CONFIGS = [(248, 248), (248, 1016), (248, 2040), (248, 4088), (504, 504), (504, 1016),
            (504, 2040), (504, 4088), (1016, 1016), (1016, 2040), (1016, 4088)]
+# tiles of 16 rows (FP32): every limit doubles plus 8
+CLASS_EDGES16 = [496, 497, 1007, 1008, 1009, 2031, 2032, 2033, 4079, 4080, 4081, 8175, 8176, 8177,
+                 9000, 1, 2, 300]
+CONFIGS16 = [(496, 496), (496, 2032), (496, 4080), (496, 8176), (1008, 1008), (1008, 2032),
+             (1008, 4080), (1008, 8176), (2032, 2032), (2032, 4080), (2032, 8176)]
 
 
-def run_cfg(lengths, dtype, cfg, seed=3):
+def run_cfg(lengths, dtype, cfg, seed=3, tile_rows=0):
     lengths = np.asarray(lengths, dtype=np.int64)
     off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
     total = int(off[-1])
@@ -169,7 +174,7 @@ def run_cfg(lengths, dtype, cfg, seed=3):
     ta, tb, tc, td = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (a, b, c, d))
     toff = torch.from_numpy(off).cuda()
     trid.solve_varlen(ta, tb, tc, td, toff, int(lengths.max()),
-                      config=trid.VarlenConfig(*cfg))
+                      config=trid.VarlenConfig(*cfg, tile_rows))
     torch.cuda.synchronize()
     return td.cpu().numpy(), ref, off
 
@@ -182,6 +187,21 @@ def test_varlen_every_class_configuration(cfg):
     assert per_system_err(got, ref, off) <= TOL[np.float32]
 
 
+@pytest.mark.parametrize("cfg", CONFIGS16, ids=[f"m16-team{a}-block{b}" for a, b in CONFIGS16])
+def test_varlen_every_class_configuration_tile16(cfg):
+    """The same with tiles of 16 rows per thread (FP32)."""
+    got, ref, off = run_cfg(CLASS_EDGES16, np.float32, cfg, tile_rows=16)
+    assert per_system_err(got, ref, off) <= TOL[np.float32]
+
+
+def test_varlen_tile16_full_batch_residual():
+    """Tiles of 16 rows on a log-uniform batch up to 16384 rows: oracle on
+    every system."""
+    lengths = inputs.loguniform_lengths(400, 16, 16384, seed=21)
+    got, ref, off = run_cfg(lengths, np.float32, (1008, 8176), seed=8, tile_rows=16)
+    assert per_system_err(got, ref, off) <= TOL[np.float32]
+
+
 def test_varlen_autotune_picks_a_valid_config_and_keeps_d():
     lengths = inputs.loguniform_lengths(600, 16, 16384, seed=9)
     off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
@@ -190,7 +210,8 @@ def test_varlen_autotune_picks_a_valid_config_and_keeps_d():
     ta, tb, tc, td = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (a, b, c, d))
     toff = torch.from_numpy(off).cuda()
     cfg, ms = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()), cache=False)
-    assert (cfg.team_max, cfg.block_max) in CONFIGS
+    assert ((cfg.team_max, cfg.block_max) in CONFIGS and cfg.tile_rows in (0, 8)) or (
+        (cfg.team_max, cfg.block_max) in CONFIGS16 and cfg.tile_rows == 16)
     assert ms > 0.0
     assert np.array_equal(td.cpu().numpy(), d)  # the autotuner works on a copy
     trid.solve_varlen(ta, tb, tc, td, toff, int(lengths.max()), config=cfg)
@@ -212,12 +233,19 @@ def test_varlen_autotune_cache_round_trip(tmp_path, monkeypatch):
     cfg1, ms1 = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()))
     assert ms1 > 0.0 and (tmp_path / "tune.json").exists()
     cfg2, ms2 = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()))
-    assert ms2 == -1.0 and (cfg2.team_max, cfg2.block_max) == (cfg1.team_max, cfg1.block_max)
+    assert ms2 == -1.0 and (cfg2.team_max, cfg2.block_max, cfg2.tile_rows or 8) == (
+        cfg1.team_max, cfg1.block_max, cfg1.tile_rows or 8)
 
 
 def test_varlen_invalid_config_rejected():
     t = torch.zeros(8, device="cuda")
     toff = torch.tensor([0, 8], dtype=torch.int64, device="cuda")
-    for bad in ((300, 4088), (1016, 504), (2040, 4088), (504, 9000)):
+    for bad in ((300, 4088, 8), (1016, 504, 8), (2040, 4088, 8), (504, 9000, 8), (1016, 4088, 16),
+                (1008, 8176, 8), (1008, 8176, 12)):
         with pytest.raises(trid.TridError):
             trid.solve_varlen(t, t + 2, t, t, toff, 8, config=trid.VarlenConfig(*bad))
+    # tiles of 16 rows are FP32 only
+    t64 = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(trid.TridError):
+        trid.solve_varlen(t64, t64 + 2, t64, t64, toff, 8,
+                          config=trid.VarlenConfig(1008, 8176, 16))
