@@ -533,6 +533,7 @@ def run_ours(args):
                        "frac": round(gbs / peaks()[0], 4),
                        "autotuned": {"team_max": vcfg.team_max, "block_max": vcfg.block_max,
                                      "tile_rows": vcfg.tile_rows or 8,
+                                     "team_warps": vcfg.team_warps or 4,
                                      "tuning_ms": round(vms, 4)},
                        "timing": "plan + persistent solve in one CUDA graph, L2 flushed"}
                 if vdt == np.float32:

@@ -288,7 +288,7 @@ trid_status trid_get_device_status(trid_stream_t stream);
 trid_status trid_wait_flag(const int *flag, int expect, double timeout_s, trid_stream_t stream);
 
 /*
- * Length classes and tile height of trid_solve_batch_varlen.  Every thread
+ * Length classes, tile height and team size of trid_solve_batch_varlen.  Every thread
  * holds tiles of tile_rows consecutive rows (M = 8, or 16 in FP32; 0 means 8).
  * Systems of up to 32 M - M rows are solved by one warp each, up to team_max
  * rows by a team of 4 warps, up to block_max rows by a whole block (512
@@ -296,15 +296,18 @@ trid_status trid_wait_flag(const int *flag, int expect, double timeout_s, trid_s
  * team_max is 248 (no team class), 504 or 1016; block_max is team_max (no
  * one-pass block class) or one of 1016, 2040, 4088 not below team_max.  With
  * M = 16 every limit doubles plus 8 (team_max 496, 1008 or 2032; block_max
- * team_max or one of 2032, 4080, 8176).  Defaults (trid_solve_batch_varlen):
- * M 8, team_max 1016, block_max 4088.  A caller zero-initialises the struct
- * and sets the fields it uses.  Not a construct of the paper (its FPGA
- * batches are uniform).
+ * team_max or one of 2032, 4080, 8176).  team_warps is the size of a team:
+ * 4 warps (0 means 4; 4 systems in flight per block) or, when team_max is
+ * 64 M - M (504 or 1008), 2 warps (8 systems in flight per block).
+ * Defaults (trid_solve_batch_varlen): M 8, team_max 1016, block_max 4088,
+ * teams of 4 warps.  A caller zero-initialises the struct and sets the fields
+ * it uses.  Not a construct of the paper (its FPGA batches are uniform).
  */
 typedef struct {
     int32_t team_max;
     int32_t block_max;
     int32_t tile_rows;
+    int32_t team_warps;
 } trid_varlen_config;
 
 /* trid_solve_batch_varlen with explicit length classes (cfg == NULL: the
@@ -316,7 +319,8 @@ trid_status trid_solve_batch_varlen_cfg(const void *a, const void *b, const void
                                         trid_stream_t stream, const trid_varlen_config *cfg);
 
 /* Autotuner: solves the caller's batch once per admissible configuration
- * (every tile height and class split above; tile height 16 in FP32 only) (on
+ * (every tile height, class split and team size above; tile height 16 in
+ * FP32 only) (on
  * a scratch copy of d inside `workspace`; a, b, c, d are not modified), times
  * each with CUDA events on `stream` (best of three after one warm-up run) and
  * writes the fastest to *best (and its time in ms to *best_ms if not NULL).

@@ -39,7 +39,8 @@ namespace trid {
 // Tile height M (rows per thread) is a template parameter: 8 (any dtype) or
 // 16 (FP32).  The class limits follow from it.
 constexpr int VL_THREADS = 512;       // threads per block of the persistent kernel
-constexpr int VL_TEAM = 128;          // threads of an M1 team
+constexpr int VL_TEAM = 128;          // threads of an M1 team (default; 64 is the other choice)
+constexpr int VL_TEAM_MIN = 64;
 constexpr int VL_BUCKETS = 40;
 constexpr int VL_PLAN_THREADS = 256;
 __host__ __device__ constexpr int vl_log2(int m) { return m == 16 ? 4 : 3; }
@@ -398,12 +399,12 @@ __global__ void __launch_bounds__(VL_THREADS, (sizeof(T) == 4 && VL_M == 8) ? 2 
 k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c, const T *d,
                T *out, int accumulate, int64_t nsys, int64_t total, int64_t max_len,
                VarlenWork *work, const longlong2 *__restrict__ meta, int nlevels, int *status,
-               int e1, int e2) {
+               int e1, int e2, int team_threads) {
     constexpr int VL_M2_N = vl_m2_n(VL_M), VL_SHORT_N = vl_short_n(VL_M);
     const int64_t m1_max = vl_class_max(e1, VL_M), m2_max = vl_class_max(e2, VL_M);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ VItem s_it[2];
-    __shared__ VItem s_team_it[VL_THREADS / VL_TEAM][2];
+    __shared__ VItem s_team_it[VL_THREADS / VL_TEAM_MIN][2];
     // level sizes for the longest admissible system (at least an M2 system)
     RLevel<T> lv[8];
     {
@@ -501,16 +502,17 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
 
     // ---- class M1: one system per team of 4 warps, tiles in registers
     {
-        const int team = tid / VL_TEAM, tt = tid % VL_TEAM;
+        const int tsz = team_threads;  // 64 or 128: 8 or 4 systems in flight per block
+        const int team = tid / tsz, tt = tid % tsz;
         const int bar = 1 + team;  // named barrier of the team (0 is __syncthreads)
-        const int thelper = VL_TEAM - 1;
+        const int thelper = tsz - 1;
         const int64_t base1 = n_l + n_m2;
-        // the team's reduced rows: R <= 2 * VL_TEAM
-        T *tbase = reinterpret_cast<T *>(smem_raw) + size_t(team) * 3 * 2 * VL_TEAM;
+        // the team's reduced rows: R <= 2 * tsz
+        T *tbase = reinterpret_cast<T *>(smem_raw) + size_t(team) * 3 * 2 * tsz;
         RLevel<T> tl;
-        tl.a = tbase; tl.c = tbase + 2 * VL_TEAM; tl.d = tbase + 4 * VL_TEAM;
+        tl.a = tbase; tl.c = tbase + 2 * tsz; tl.d = tbase + 4 * tsz;
         if (tt == thelper) s_team_it[team][0] = vitem_fetch(&work->next_m1, n_m1, base1, meta);
-        named_barrier_sync(bar, VL_TEAM);
+        named_barrier_sync(bar, tsz);
         for (int cur = 0;; cur ^= 1) {
             const VItem it = s_team_it[team][cur];
             if (it.item >= n_m1) break;
@@ -520,7 +522,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             const bool ok = sys_valid(s0, n, total) && n <= m1_max;
             if (!ok && tt == 0 && status) atomicCAS(status, 0, int(TRID_ERR_INVALID_ARG));
             const int pad = sys_pad<T>(s0);
-            const int ntiles = ok ? int((n + pad + VL_M - 1) / VL_M) : 0;  // <= VL_TEAM
+            const int ntiles = ok ? int((n + pad + VL_M - 1) / VL_M) : 0;  // <= tsz
             const bool mine = tt < ntiles;
             T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
             tl.R = 2 * ntiles;
@@ -533,16 +535,16 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             }
             longlong2 nx_meta = make_longlong2(0, 0);
             if (tt == thelper && (long long)nx_item < n_m1) nx_meta = meta[base1 + nx_item];
-            named_barrier_sync(bar, VL_TEAM);
+            named_barrier_sync(bar, tsz);
             if (ok && tt < 32) level_warp_solve<T, VL_M>(tl);
             if (tt == thelper)
                 s_team_it[team][cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
-            named_barrier_sync(bar, VL_TEAM);
+            named_barrier_sync(bar, tsz);
             if (mine) {
                 tile_substitute<T, VL_M>(ra, rc, rd, tl.d[2 * tt], tl.d[2 * tt + 1]);
                 store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, tt, rd);
             }
-            named_barrier_sync(bar, VL_TEAM);  // the team's rows are rewritten next
+            named_barrier_sync(bar, tsz);  // the team's rows are rewritten next
         }
     }
 
@@ -606,7 +608,7 @@ static bool varlen_levels(int64_t max_len, int &nlevels, size_t &smem) {
 template <typename T, int VL_M>
 static trid_status varlen_run(const T *a, const T *b, const T *c, const T *d, T *out, int acc,
                               const int64_t *offsets, int64_t nsys, int64_t total, int64_t max_len,
-                              void *ws, cudaStream_t st, int e1, int e2) {
+                              void *ws, cudaStream_t st, int e1, int e2, int team_threads) {
     int nlevels = 0;
     size_t smem = 0;
     if (!varlen_levels<T, VL_M>(max_len, nlevels, smem)) return TRID_ERR_UNSUPPORTED;
@@ -631,7 +633,8 @@ static trid_status varlen_run(const T *a, const T *b, const T *c, const T *d, T 
     int64_t grid = int64_t(di->sm_count) * per_sm;
     kern<<<dim3(unsigned(grid)), VL_THREADS, smem, st>>>(a, b, c, d, out, acc, nsys, total,
                                                          max_len, work, meta, nlevels,
-                                                         device_status_word(), e1, e2);
+                                                         device_status_word(), e1, e2,
+                                                         team_threads);
     return cudaGetLastError() == cudaSuccess ? TRID_OK : TRID_ERR_CUDA;
 }
 
@@ -646,8 +649,10 @@ extern "C" size_t trid_solve_varlen_workspace_bytes(int64_t nsys) {
 
 // Tile height and class edges of a configuration (see trid_varlen_config in
 // include/trid.h); false for a configuration outside the admissible list.
-static bool vl_edges(const trid_varlen_config *cfg, trid_dtype dtype, int &m, int &e1, int &e2) {
+static bool vl_edges(const trid_varlen_config *cfg, trid_dtype dtype, int &m, int &e1, int &e2,
+                     int &team_threads) {
     m = 8;
+    team_threads = VL_TEAM;
     if (cfg && cfg->tile_rows != 0 && cfg->tile_rows != 8) {
         if (cfg->tile_rows != 16 || dtype != TRID_F32) return false;
         m = 16;
@@ -663,6 +668,11 @@ static bool vl_edges(const trid_varlen_config *cfg, trid_dtype dtype, int &m, in
     else if (!edge_of(cfg->team_max, e1) || e1 > e1max) return false;
     if (cfg->block_max == cfg->team_max) e2 = e1;
     else if (!edge_of(cfg->block_max, e2) || e2 > e2max || e2 < e1) return false;
+    if (cfg->team_warps != 0 && cfg->team_warps != 4) {
+        // teams of 2 warps: only for a team class that fits them
+        if (cfg->team_warps != 2 || e1 != lo + 1) return false;
+        team_threads = VL_TEAM_MIN;
+    }
     return true;
 }
 
@@ -673,8 +683,8 @@ static trid_status varlen_entry(const void *a, const void *b, const void *c, voi
                                 const trid_varlen_config *cfg) {
     if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
     if (nsys < 0 || total < 0 || max_len < 0) return TRID_ERR_INVALID_ARG;
-    int m, e1, e2;
-    if (!vl_edges(cfg, dtype, m, e1, e2)) return TRID_ERR_INVALID_ARG;
+    int m, e1, e2, tt;
+    if (!vl_edges(cfg, dtype, m, e1, e2, tt)) return TRID_ERR_INVALID_ARG;
     if (nsys == 0 || total == 0) return TRID_OK;
     if (!a || !b || !c || !d || !offsets) return TRID_ERR_INVALID_ARG;
     const size_t esz = dtype == TRID_F32 ? 4 : 8;
@@ -702,14 +712,14 @@ static trid_status varlen_entry(const void *a, const void *b, const void *c, voi
         float *fo = static_cast<float *>(u ? u : d);
         if (m == 16)
             return varlen_run<float, 16>(fa, fb, fc, fd, fo, acc, offsets, nsys, total, max_len,
-                                         workspace, st, e1, e2);
+                                         workspace, st, e1, e2, tt);
         return varlen_run<float, 8>(fa, fb, fc, fd, fo, acc, offsets, nsys, total, max_len,
-                                    workspace, st, e1, e2);
+                                    workspace, st, e1, e2, tt);
     }
     return varlen_run<double, 8>(static_cast<const double *>(a), static_cast<const double *>(b),
                               static_cast<const double *>(c), static_cast<const double *>(d),
                               static_cast<double *>(u ? u : d), acc, offsets, nsys, total,
-                              max_len, workspace, st, e1, e2);
+                              max_len, workspace, st, e1, e2, tt);
 }
 
 extern "C" trid_status trid_solve_batch_varlen(const void *a, const void *b, const void *c,
@@ -753,6 +763,7 @@ extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const 
     best->team_max = int32_t(vl_class_max(vl_e1_default(8), 8));
     best->block_max = int32_t(vl_class_max(vl_e2_default(8), 8));
     best->tile_rows = 8;
+    best->team_warps = 4;
     if (best_ms) *best_ms = 0.0f;
     if (dtype != TRID_F32 && dtype != TRID_F64) return TRID_ERR_INVALID_ARG;
     if (nsys < 0 || total < 0 || max_len < 0) return TRID_ERR_INVALID_ARG;
@@ -783,10 +794,11 @@ extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const 
                                int32_t(vl_class_max(vl_b_m1(m) + 4, m)), 0};
     for (int ti = 0; ti < 3 && rs == TRID_OK; ++ti) {
         for (int bi = 0; bi < 4 && rs == TRID_OK; ++bi) {
+        for (int tw = 4; tw >= 2 && rs == TRID_OK; tw -= 2) {  // warps per team
             if (bi < 3 && blocks[bi] == teams[ti]) continue;  // same as bi == 3
-            trid_varlen_config cfg{teams[ti], bi == 3 ? teams[ti] : blocks[bi], m};
-            int mm, ea, eb;
-            if (!vl_edges(&cfg, dtype, mm, ea, eb)) continue;
+            trid_varlen_config cfg{teams[ti], bi == 3 ? teams[ti] : blocks[bi], m, tw};
+            int mm, ea, eb, tt;
+            if (!vl_edges(&cfg, dtype, mm, ea, eb, tt)) continue;
             float t_best = -1.0f;
             for (int rep = 0; rep < 4 && rs == TRID_OK; ++rep) {  // first run warms up
                 if (cudaMemcpyAsync(scratch, d, size_t(total) * esz, cudaMemcpyDeviceToDevice,
@@ -805,6 +817,7 @@ extern "C" trid_status trid_varlen_autotune(const void *a, const void *b, const 
                 best_t = t_best;
                 *best = cfg;
             }
+        }
         }
     }
     }

@@ -197,14 +197,14 @@ def varlen_workspace_bytes(nsys: int) -> int:
 
 
 class VarlenConfig(ctypes.Structure):
-    """Length classes and tile height of the uneven-batch solver
-    (trid_varlen_config; tile_rows 0 means 8)."""
+    """Length classes, tile height and team size of the uneven-batch solver
+    (trid_varlen_config; tile_rows 0 means 8, team_warps 0 means 4)."""
     _fields_ = [("team_max", ctypes.c_int32), ("block_max", ctypes.c_int32),
-                ("tile_rows", ctypes.c_int32)]
+                ("tile_rows", ctypes.c_int32), ("team_warps", ctypes.c_int32)]
 
     def __repr__(self):
         return (f"VarlenConfig(team_max={self.team_max}, block_max={self.block_max}, "
-                f"tile_rows={self.tile_rows or 8})")
+                f"tile_rows={self.tile_rows or 8}, team_warps={self.team_warps or 4})")
 
 
 def _check_offsets(offsets):
@@ -285,7 +285,7 @@ def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None, cache: bool 
         hit = table.get(key)
         if hit is not None:
             return VarlenConfig(int(hit["team_max"]), int(hit["block_max"]),
-                                int(hit.get("tile_rows", 8))), -1.0
+                                int(hit.get("tile_rows", 8)), int(hit.get("team_warps", 4))), -1.0
     L = load()
     ws = torch.empty(max(int(L.trid_varlen_autotune_workspace_bytes(nsys, total, _dtype(d))), 1),
                      dtype=torch.uint8, device=d.device)
@@ -299,7 +299,8 @@ def varlen_autotune(a, b, c, d, offsets, max_len: int, stream=None, cache: bool 
         raise TridError(st, "trid_varlen_autotune")
     if cache:
         table[key] = {"team_max": int(best.team_max), "block_max": int(best.block_max),
-                      "tile_rows": int(best.tile_rows or 8), "ms": float(ms.value)}
+                      "tile_rows": int(best.tile_rows or 8),
+                      "team_warps": int(best.team_warps or 4), "ms": float(ms.value)}
         path = _tune_cache_path()
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)

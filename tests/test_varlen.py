@@ -194,6 +194,26 @@ def test_varlen_every_class_configuration_tile16(cfg):
     assert per_system_err(got, ref, off) <= TOL[np.float32]
 
 
+TEAM2 = [((504, 504), 8), ((504, 4088), 8), ((1008, 8176), 16), ((1008, 1008), 16)]
+
+
+@pytest.mark.parametrize("cfg,m", TEAM2, ids=[f"m{m}-team{a}-block{b}-2warps" for (a, b), m in TEAM2])
+def test_varlen_two_warp_teams(cfg, m):
+    """Teams of 2 warps (8 systems in flight per block) for the smaller team
+    class, with either tile height."""
+    lengths = (CLASS_EDGES if m == 8 else CLASS_EDGES16) + [100, 400, 503, 504, 1000]
+    lengths = np.asarray(lengths, dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    total = int(off[-1])
+    a, b, c, d = inputs.dominant_system((total,), seed=4, dtype=np.float32)
+    ref = oracle.solve_varlen(a, b, c, d, off)
+    ta, tb, tc, td = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (a, b, c, d))
+    trid.solve_varlen(ta, tb, tc, td, torch.from_numpy(off).cuda(), int(lengths.max()),
+                      config=trid.VarlenConfig(*cfg, m, 2))
+    torch.cuda.synchronize()
+    assert per_system_err(td.cpu().numpy(), ref, off) <= TOL[np.float32]
+
+
 def test_varlen_tile16_full_batch_residual():
     """Tiles of 16 rows on a log-uniform batch up to 16384 rows: oracle on
     every system."""
@@ -212,6 +232,7 @@ def test_varlen_autotune_picks_a_valid_config_and_keeps_d():
     cfg, ms = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()), cache=False)
     assert ((cfg.team_max, cfg.block_max) in CONFIGS and cfg.tile_rows in (0, 8)) or (
         (cfg.team_max, cfg.block_max) in CONFIGS16 and cfg.tile_rows == 16)
+    assert cfg.team_warps in (0, 4) or (cfg.team_warps == 2 and cfg.team_max in (504, 1008))
     assert ms > 0.0
     assert np.array_equal(td.cpu().numpy(), d)  # the autotuner works on a copy
     trid.solve_varlen(ta, tb, tc, td, toff, int(lengths.max()), config=cfg)
@@ -233,15 +254,17 @@ def test_varlen_autotune_cache_round_trip(tmp_path, monkeypatch):
     cfg1, ms1 = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()))
     assert ms1 > 0.0 and (tmp_path / "tune.json").exists()
     cfg2, ms2 = trid.varlen_autotune(ta, tb, tc, td, toff, int(lengths.max()))
-    assert ms2 == -1.0 and (cfg2.team_max, cfg2.block_max, cfg2.tile_rows or 8) == (
-        cfg1.team_max, cfg1.block_max, cfg1.tile_rows or 8)
+    assert ms2 == -1.0 and (cfg2.team_max, cfg2.block_max, cfg2.tile_rows or 8,
+                            cfg2.team_warps or 4) == (cfg1.team_max, cfg1.block_max,
+                                                      cfg1.tile_rows or 8, cfg1.team_warps or 4)
 
 
 def test_varlen_invalid_config_rejected():
     t = torch.zeros(8, device="cuda")
     toff = torch.tensor([0, 8], dtype=torch.int64, device="cuda")
     for bad in ((300, 4088, 8), (1016, 504, 8), (2040, 4088, 8), (504, 9000, 8), (1016, 4088, 16),
-                (1008, 8176, 8), (1008, 8176, 12)):
+                (1008, 8176, 8), (1008, 8176, 12), (1016, 4088, 8, 2), (248, 4088, 8, 2),
+                (504, 4088, 8, 3)):
         with pytest.raises(trid.TridError):
             trid.solve_varlen(t, t + 2, t, t, toff, 8, config=trid.VarlenConfig(*bad))
     # tiles of 16 rows are FP32 only
