@@ -98,31 +98,10 @@ struct XFold {
     T fr[4], fae[4], fce[4], xas[4], xcs[4];
 };
 
-__device__ __forceinline__ void cluster_arrive_release() {
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void cluster_wait_acquire() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// Address of the same shared-memory location in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t cluster_map(uint32_t saddr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ float ld_cluster_f32(uint32_t addr) {
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-    return v;
-}
 
-// Store to the shared memory of another CTA of the cluster; the bytes count
-// towards the transaction count of an mbarrier in that CTA.
-__device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t bar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];"
-                 ::"r"(addr), "f"(v), "r"(bar)
-                 : "memory");
-}
 __device__ __forceinline__ void cluster_arrive_relaxed() {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
@@ -151,15 +130,6 @@ __device__ __forceinline__ void win_solve_k(float (&v)[W], const WinTab<float, W
     }
 }
 
-template <int W, int lo>
-__device__ __forceinline__ void win_solve(float (&v)[W], const WinTab<float, W> &tab, int kind) {
-    switch (kind) {  // uniform across the warp
-        case 0: win_solve_k<0, W, lo>(v, tab); break;
-        case 1: win_solve_k<1, W, lo>(v, tab); break;
-        case 2: win_solve_k<2, W, lo>(v, tab); break;
-        default: win_solve_k<3, W, lo>(v, tab); break;
-    }
-}
 
 // The tile's part of the split window solve for kind K: Thomas over the 32
 // tile rows with zero halos (x_40 = R f_39).

@@ -19,9 +19,11 @@
 //  2. tile_reduce, then one warp per system solves the chunk's reduced
 //     system (PCR over 32 tiles, as group_solve) for p, q and r at once:
 //     every tile end's p, q, r value stays in the solving lane's registers.
-//  3. The values at the chunk's first row (F) and last row (E) go to shared
-//     memory; after a cluster barrier every CTA gathers all C chunks' values
-//     through distributed shared memory and solves the chunk-level system
+//  3. The values at the chunk's first row (F) and last row (E) are sent to
+//     every CTA of the cluster (st.async into its shared memory, counted on
+//     an mbarrier there, one per strip parity: no cluster barrier per strip);
+//     once all C chunks' values have landed, every CTA solves the chunk-level
+//     system
 //         F_k = P0_k + Q0_k E_{k-1} + R0_k F_{k+1}
 //         E_k = P1_k + Q1_k E_{k-1} + R1_k F_{k+1}
 //     (2x2 block elimination, one thread per system) for its own x_L and x_R.
@@ -44,8 +46,9 @@ constexpr int CK_THREADS = CK_NT * CK_SG;
 constexpr int CK_MAX_CHUNKS = 8;     // cluster size (portable)
 
 // Shared memory: the chunk's box of 4 arrays, the reduced tables (6 rows + 2
-// solutions per tile, row pitch SG + 1), two buffers of F/E values (6 x SG),
-// the gathered values of all chunks (C x 6 x SG) and the mbarrier.
+// solutions per tile, row pitch SG + 1), the received values of all chunks
+// per strip parity (2 x C x 6 x SG), x_L and x_R, and the mbarriers (box
+// landed; values of parity 0 and 1 landed).
 // CM rows per thread: chunks of CK_NT * CM rows (256 or 512).
 template <typename T, int CM>
 struct ChunkLayout {
@@ -53,14 +56,13 @@ struct ChunkLayout {
     static constexpr int ROWS = CK_NT * CM;
     __host__ __device__ static size_t slot_bytes() { return size_t(ROWS) * CK_SG * sizeof(T); }
     __host__ __device__ static size_t tab_off() { return 4 * slot_bytes(); }
-    __host__ __device__ static size_t spk_off() { return tab_off() + 8 * CK_NT * P * sizeof(T); }
-    __host__ __device__ static size_t gat_off() { return spk_off() + 2 * 6 * CK_SG * sizeof(T); }
+    __host__ __device__ static size_t gat_off() { return tab_off() + 8 * CK_NT * P * sizeof(T); }
     __host__ __device__ static size_t bar_off(int C) {
-        return (gat_off() + size_t(C) * 6 * CK_SG * sizeof(T) + 2 * 2 * CK_SG * sizeof(T) + 15) /
-               16 * 16;
+        return (gat_off() + 2 * size_t(C) * 6 * CK_SG * sizeof(T) + 2 * 2 * CK_SG * sizeof(T) +
+                15) / 16 * 16;
     }
     // x staging for the TMA store of the chunk (same [row][SG] layout)
-    __host__ __device__ static size_t xst_off(int C) { return (bar_off(C) + 16 + 127) / 128 * 128; }
+    __host__ __device__ static size_t xst_off(int C) { return (bar_off(C) + 32 + 127) / 128 * 128; }
     __host__ __device__ static size_t bytes(int C) { return xst_off(C) + slot_bytes(); }
 };
 
@@ -142,10 +144,10 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
     T *s_as = tab, *s_cs = tab + NT * P, *s_ds = tab + 2 * NT * P;
     T *s_ae = tab + 3 * NT * P, *s_ce = tab + 4 * NT * P, *s_de = tab + 5 * NT * P;
     T *s_xs = tab + 6 * NT * P, *s_xe = tab + 7 * NT * P;
-    T *spk = reinterpret_cast<T *>(smem + LY::spk_off());     // [2][6][SG]
-    T *gat = reinterpret_cast<T *>(smem + LY::gat_off());     // [C][6][SG]
-    T *xlr = gat + size_t(C) * 6 * SG;                        // [2][SG]: x_L, x_R
+    T *gat = reinterpret_cast<T *>(smem + LY::gat_off());     // [2][C][6][SG]
+    T *xlr = gat + 2 * size_t(C) * 6 * SG;                    // [2][SG]: x_L, x_R
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + LY::bar_off(C));
+    uint64_t *gbar = full + 1;  // [2]: all chunks' values of a strip parity landed
     T *xst = reinterpret_cast<T *>(smem + LY::xst_off(C));
 
     __shared__ int abort_flag;
@@ -155,10 +157,12 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
     if (tid == 0) {
         abort_flag = 0;
         mbar_init(full, 1);
+        mbar_init(&gbar[0], 1);
+        mbar_init(&gbar[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    cluster.sync();  // every peer has started before its shared memory is read
+    cluster.sync();  // every peer's mbarriers are initialised before values are sent to it
 
     const uint32_t tx = 4u * uint32_t(CH) * SG * sizeof(T);
     auto issue = [&](int strip) {
@@ -182,6 +186,10 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
     const int stride = int(L.stride);
     int j = 0;
     for (int strip = cid; strip < nstrips; strip += ncl, ++j) {
+        T *gj = gat + size_t(j & 1) * C * 6 * SG;  // this strip's received values
+        // this CTA's arrival on the parity's mbarrier, with the bytes that the C
+        // chunks (itself included) will send
+        if (tid == 0) mbar_expect_tx(&gbar[j & 1], uint32_t(C) * 6 * SG * uint32_t(sizeof(T)));
         bool ok = false;
         if (!*(volatile int *)&abort_flag) {
             ok = mbar_wait(full, uint32_t(j) & 1u, status);
@@ -218,23 +226,29 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
             group_solve_spikes<T>(qas, qcs, s_ds[q], qae, qce, s_de[q], rt, ps, pe, us, ue, vs,
                                   ve);
         }
-        T *sp = spk + (j & 1) * 6 * SG;
-        if (rt == 0) { sp[0 * SG + rs] = ps; sp[2 * SG + rs] = us; sp[4 * SG + rs] = vs; }
-        if (rt == NT - 1) { sp[1 * SG + rs] = pe; sp[3 * SG + rs] = ue; sp[5 * SG + rs] = ve; }
-        cluster.sync();
-        // gather the F/E values of every chunk of the strip
-        for (int t = tid; t < C * 6 * SG; t += CK_THREADS) {
-            const int r = t / (6 * SG);
-            const T *peer = cluster.map_shared_rank(sp, r);
-            gat[t] = peer[t - r * 6 * SG];
+        // send this chunk's F (first tile) and E (last tile) values to slot
+        // `rank` of every CTA of the cluster
+        if (rt == 0 || rt == NT - 1) {
+            const int row = rt == 0 ? 0 : 1;
+            const T v0 = rt == 0 ? ps : pe, v1 = rt == 0 ? us : ue, v2 = rt == 0 ? vs : ve;
+            const uint32_t loc = smem_u32(gj + size_t(rank) * 6 * SG + row * SG + rs);
+            const uint32_t lbar = smem_u32(&gbar[j & 1]);
+            for (int r = 0; r < C; ++r) {
+                const uint32_t dst = cluster_map(loc, uint32_t(r));
+                const uint32_t bar = cluster_map(lbar, uint32_t(r));
+                st_async_f32(dst, v0, bar);
+                st_async_f32(dst + 2u * SG * uint32_t(sizeof(T)), v1, bar);
+                st_async_f32(dst + 4u * SG * uint32_t(sizeof(T)), v2, bar);
+            }
         }
-        __syncthreads();
+        // every chunk's values of this strip have landed (bounded wait)
+        if (!mbar_wait(&gbar[j & 1], uint32_t(j >> 1) & 1u, status)) *(volatile int *)&abort_flag = 1;
         if (tid < SG) {
             // chunk-level system of system `tid`: forward elimination
             // E_k = al_k + be_k F_{k+1}, F_k = ga_k + de_k F_{k+1}
             T al = T(0), be = T(0);
             for (int k = 0; k < C; ++k) {
-                T *g = gat + size_t(k) * 6 * SG + tid;
+                T *g = gj + size_t(k) * 6 * SG + tid;
                 const T p0 = g[0], p1 = g[SG], q0 = g[2 * SG], q1 = g[3 * SG];
                 const T r0 = g[4 * SG], r1 = g[5 * SG];
                 const T inv = rcp(T(1) - q0 * be);
@@ -248,7 +262,7 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
             // back substitution from F_C = 0 down to this chunk
             T fnext = T(0), xl = T(0), xr = T(0);
             for (int k = C - 1; k >= rank - 1 && k >= 0; --k) {
-                const T *g = gat + size_t(k) * 6 * SG + tid;
+                const T *g = gj + size_t(k) * 6 * SG + tid;
                 if (k == rank) xr = fnext;
                 if (k == rank - 1) xl = g[SG] + g[5 * SG] * fnext;  // E_{rank-1}
                 fnext = g[0] + g[4 * SG] * fnext;                   // F_k
@@ -298,7 +312,7 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
         }
     }
     if (tma_store && tid == 0) bulk_wait_all();  // every store of this CTA has landed
-    cluster.sync();  // no CTA leaves while a peer may still read its values
+    cluster.sync();  // no CTA leaves while values it sent may still be in flight
 }
 
 }  // namespace trid
