@@ -12,13 +12,18 @@
 // With kappa = 1 this is the constant-coefficient 2D step.
 //
 // Reverse mode of one step, g = dL/du_{t+1}:
-//   g_w = Y^{-T} g and g_d = X^{-T} g_w   (trid_solve_batch_adjoint, which
-//        also gives the coefficient gradients -g_w delta_{p-nx}, ...),
+//   g_w = Y^{-T} g and g_d = X^{-T} g_w, with the coefficient gradients of
+//        the solves -g_w delta_{p-nx}, -g_w delta_p, -g_w delta_{p+nx} (Y) and
+//        -g_d w_{p-1}, -g_d w_p, -g_d w_{p+1} (X),
 //   g_d restricted to the interior, dL/du_t = g + (transposed stencil) g_d,
 //   and the stencil adds g_d (u_p - u_{p-1}) to the gradient of a_p and
 //   g_d (u_p - u_{p+1}) to that of c_p (y alike).
-// The coefficient arrays do not change over the steps, so their gradients are
-// summed over the steps and taken to kappa once at the end.
+// The coefficient arrays do not change over the steps: the transposed
+// operators (sub-diagonal c_{i-1}, super-diagonal a_{i+1}) are formed once
+// per backward call, each step's two adjoint solves are plain solves of them
+// accumulated into zeroed buffers (so g and g_w stay intact), and one kernel
+// per step forms the stencil's reverse, every coefficient gradient of the step
+// and their sums over the steps (taken to kappa once at the end).
 //
 // Checkpointing: the forward keeps u every `every` steps; the backward
 // recomputes each segment forward from its checkpoint (keeping u_t, w_t and
@@ -76,25 +81,65 @@ __global__ void k_v2_rhs(const T *__restrict__ u, const T *__restrict__ ax,
     }
 }
 
+// The transposed operators: A^T has sub-diagonal c_{i-1} and super-diagonal
+// a_{i+1} (the diagonal is b).
 template <typename T>
-__global__ void k_v2_add(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out,
-                         size_t n) {
-    for (size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
-         p += size_t(gridDim.x) * blockDim.x)
-        out[p] = a[p] + b[p];
+__global__ void k_v2_transpose(const T *__restrict__ ax, const T *__restrict__ cx,
+                               const T *__restrict__ ay, const T *__restrict__ cy, T *atx, T *ctx,
+                               T *aty, T *cty, int nx, int ny) {
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= nx) continue;
+        const size_t p = size_t(j) * nx + i;
+        atx[p] = i > 0 ? cx[p - 1] : T(0);
+        ctx[p] = i < nx - 1 ? ax[p + 1] : T(0);
+        aty[p] = j > 0 ? cy[p - nx] : T(0);
+        cty[p] = j < ny - 1 ? ay[p + nx] : T(0);
+    }
+}
+
+// The explicit part of a recomputed step, from the previous step's state and
+// increment: u = up + dp (when dp is given; else u is read as is), written to
+// u; d = lam (Lx + Ly) u as k_v2_rhs; dz zeroed (the step's delta, which the
+// y solve then accumulates into).
+template <typename T>
+__global__ void k_v2_rhs_keep(const T *__restrict__ up, const T *__restrict__ dp, T *u,
+                              const T *__restrict__ ax, const T *__restrict__ cx,
+                              const T *__restrict__ ay, const T *__restrict__ cy,
+                              T *__restrict__ d, T *__restrict__ dz, int nx, int ny) {
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= nx) continue;
+        const size_t p = size_t(j) * nx + i;
+        auto U = [&](size_t q) -> T { return dp ? up[q] + dp[q] : u[q]; };
+        const T uc = U(p);
+        T v = T(0);
+        if (i > 0 && i < nx - 1 && j > 0 && j < ny - 1) {
+            v = -cx[p] * (U(p + 1) - uc) + ax[p] * (uc - U(p - 1));
+            v += -cy[p] * (U(p + nx) - uc) + ay[p] * (uc - U(p - nx));
+        }
+        d[p] = v;
+        dz[p] = T(0);
+        if (dp) u[p] = uc;
+    }
 }
 
 // Reverse of the explicit part and of the identity path, plus the summed
 // coefficient gradients:  gn = g + S^T gm  (gm = g_d on the interior),
-// G_k += (step gradient k) + stencil term.  Gather form: point q collects the
-// stencil rows p = q, q +- 1, q +- nx that read u_q.
+// G_k += (gradient of coefficient k through the two solves) + stencil term.
+// Gather form: point q collects the stencil rows p = q, q +- 1, q +- nx that
+// read u_q.  w and dl are the step's X^{-1} d and delta; gd_next and gw_next
+// (the other buffers of the pair) are zeroed for the next step's accumulating
+// adjoint solves.
 template <typename T>
 __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
-                             const T *__restrict__ u, const T *__restrict__ ax,
-                             const T *__restrict__ cx, const T *__restrict__ ay,
-                             const T *__restrict__ cy, const T *__restrict__ sg, T *__restrict__ G,
-                             T *__restrict__ gn, int nx, int ny, size_t n) {
-    // n: element stride between the six arrays of sg and of G
+                             const T *__restrict__ gw, const T *__restrict__ u,
+                             const T *__restrict__ w, const T *__restrict__ dl,
+                             const T *__restrict__ ax, const T *__restrict__ cx,
+                             const T *__restrict__ ay, const T *__restrict__ cy, T *__restrict__ G,
+                             T *__restrict__ gn, T *__restrict__ gd_next, T *__restrict__ gw_next,
+                             int nx, int ny, size_t n) {
+    // n: element stride between the six arrays of G
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= nx) continue;
@@ -110,9 +155,16 @@ __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
         if (j > 0) acc -= cy[p - nx] * gm(i, j - 1);
         if (j < ny - 1) acc -= ay[p + nx] * gm(i, j + 1);
         gn[p] = acc;
-        // summed coefficient gradients: ax, bx, cx, ay, by, cy
+        // coefficient gradients of the x solve (w = X^{-1} d) and of the y
+        // solve (delta = Y^{-1} w), then the stencil's terms
+        const T gdp = gd[p], gwp = gw[p];
+        T sa = i > 0 ? -gdp * w[p - 1] : T(0);
+        const T sb = -gdp * w[p];
+        T sc = i < nx - 1 ? -gdp * w[p + 1] : T(0);
+        T ta = j > 0 ? -gwp * dl[p - nx] : T(0);
+        const T tb = -gwp * dl[p];
+        T tc = j < ny - 1 ? -gwp * dl[p + nx] : T(0);
         const T uc = u[p];
-        T sa = sg[p], sc = sg[2 * n + p], ta = sg[3 * n + p], tc = sg[5 * n + p];
         if (g0 != T(0)) {
             sa += g0 * (uc - u[p - 1]);
             sc += g0 * (uc - u[p + 1]);
@@ -120,11 +172,13 @@ __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
             tc += g0 * (uc - u[p + nx]);
         }
         G[p] += sa;
-        G[n + p] += sg[n + p];
+        G[n + p] += sb;
         G[2 * n + p] += sc;
         G[3 * n + p] += ta;
-        G[4 * n + p] += sg[4 * n + p];
+        G[4 * n + p] += tb;
         G[5 * n + p] += tc;
+        gd_next[p] = T(0);
+        gw_next[p] = T(0);
     }
 }
 
@@ -188,8 +242,9 @@ static bool v2_layout(const int64_t *dims, int nsteps, int every, trid_dtype dty
     l.scratch = up256(s);
     const size_t K = size_t(every);
     l.fwd = 7 * l.mesh + l.scratch;  // 6 coefficient arrays + d/w
-    // coefficients 6, segment u/w/delta 3K, g, gn, g_w, g_d 4, step grads 6, sums 6
-    l.bwd = (6 + 3 * K + 4 + 6 + 6) * l.mesh + l.scratch;
+    // coefficients 6, transposed coefficients 4, segment u/w/delta 3K, g and gn 2,
+    // two g_w and two g_d 4, sums 6
+    l.bwd = (6 + 4 + 3 * K + 2 + 4 + 6) * l.mesh + l.scratch;
     l.nseg = nsteps == 0 ? 1 : (nsteps + every - 1) / every;
     return true;
 }
@@ -202,33 +257,38 @@ static void grid2(int nx, int ny, dim3 &g, dim3 &b) {
 
 template <typename T>
 static trid_status v2_forward_step(T *u, T *dw, const T *const co[6], const int64_t *dims,
-                                   char *scr, size_t scr_bytes, trid_dtype dt, cudaStream_t st,
-                                   T *w_keep = nullptr, T *delta_keep = nullptr,
-                                   T *u_next = nullptr) {
+                                   char *scr, size_t scr_bytes, trid_dtype dt, cudaStream_t st) {
     const int nx = int(dims[0]), ny = int(dims[1]);
     dim3 g, b;
     grid2<T>(nx, ny, g, b);
-    T *w = w_keep ? w_keep : dw;
-    k_v2_rhs<T><<<g, b, 0, st>>>(u, co[0], co[2], co[3], co[5], w, nx, ny);
+    k_v2_rhs<T><<<g, b, 0, st>>>(u, co[0], co[2], co[3], co[5], dw, nx, ny);
+    if (!launch_ok()) return TRID_ERR_CUDA;
+    trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], dw, nullptr, dims, 2, 0, dt, scr,
+                                        scr_bytes, st);
+    if (s != TRID_OK) return s;
+    // u += Y^{-1} w
+    return trid_solve_batch_ws(co[3], co[4], co[5], dw, u, dims, 2, 1, dt, scr, scr_bytes, st);
+}
+
+// A step recomputed by the backward, keeping u (at u; formed from the
+// previous state up and increment dp unless dp is NULL), w = X^{-1} d (at w)
+// and delta = Y^{-1} w (at dl).  Three launches: the explicit part (which also
+// writes u and zeroes dl), the x solve in place, the y solve accumulated into
+// dl (w stays intact).  u + delta is formed by the next step's first kernel,
+// with the same rounding as the forward's accumulating y solve.
+template <typename T>
+static trid_status v2_recompute_step(const T *up, const T *dp, T *u, T *w, T *dl,
+                                     const T *const co[6], const int64_t *dims, char *scr,
+                                     size_t scr_bytes, trid_dtype dt, cudaStream_t st) {
+    const int nx = int(dims[0]), ny = int(dims[1]);
+    dim3 g, b;
+    grid2<T>(nx, ny, g, b);
+    k_v2_rhs_keep<T><<<g, b, 0, st>>>(up, dp, u, co[0], co[2], co[3], co[5], w, dl, nx, ny);
     if (!launch_ok()) return TRID_ERR_CUDA;
     trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], w, nullptr, dims, 2, 0, dt, scr,
                                         scr_bytes, st);
     if (s != TRID_OK) return s;
-    if (!delta_keep) {
-        // u += Y^{-1} w
-        return trid_solve_batch_ws(co[3], co[4], co[5], w, u, dims, 2, 1, dt, scr, scr_bytes, st);
-    }
-    const size_t n = size_t(nx) * ny;
-    if (cudaMemcpyAsync(delta_keep, w, n * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-        return launch_ok(), TRID_ERR_CUDA;
-    s = trid_solve_batch_ws(co[3], co[4], co[5], delta_keep, nullptr, dims, 2, 1, dt, scr,
-                            scr_bytes, st);
-    if (s != TRID_OK) return s;
-    if (u_next) {
-        k_v2_add<T><<<1024, 256, 0, st>>>(u, delta_keep, u_next, n);
-        if (!launch_ok()) return TRID_ERR_CUDA;
-    }
-    return TRID_OK;
+    return trid_solve_batch_ws(co[3], co[4], co[5], w, dl, dims, 2, 1, dt, scr, scr_bytes, st);
 }
 
 template <typename T>
@@ -272,23 +332,31 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     T *base = reinterpret_cast<T *>(ws);
     T *co[6];
     for (int k = 0; k < 6; ++k) co[k] = base + k * ms;
+    T *tr = base + 6 * ms;           // transposed x (a, c), transposed y (a, c)
     const int K = every;
-    T *U = base + 6 * ms;            // K states
+    T *U = tr + 4 * ms;              // K states
     T *W = U + size_t(K) * ms;       // K
     T *D = W + size_t(K) * ms;       // K
     T *g = D + size_t(K) * ms;
-    T *gn = g + ms, *gw = gn + ms, *gd = gw + ms;
-    T *sg = gd + ms;                 // 6 step gradients (ax, bx, cx, ay, by, cy)
-    T *G = sg + 6 * ms;              // 6 sums
-    char *scr = ws + (6 + 3 * size_t(K) + 4 + 6 + 6) * l.mesh;
+    T *gn = g + ms;
+    T *gwb[2] = {gn + ms, gn + 2 * ms};  // g_w, double-buffered
+    T *gdb[2] = {gn + 3 * ms, gn + 4 * ms};  // g_d, double-buffered
+    T *G = gn + 5 * ms;              // 6 sums
+    char *scr = ws + (6 + 4 + 3 * size_t(K) + 2 + 4 + 6) * l.mesh;
     dim3 g2, b2;
     grid2<T>(nx, ny, g2, b2);
     k_v2_coef<T><<<g2, b2, 0, st>>>(kap, co[0], co[1], co[2], co[3], co[4], co[5], nx, ny, lam);
+    k_v2_transpose<T><<<g2, b2, 0, st>>>(co[0], co[2], co[3], co[5], tr, tr + ms, tr + 2 * ms,
+                                         tr + 3 * ms, nx, ny);
     if (!launch_ok()) return TRID_ERR_CUDA;
     if (cudaMemsetAsync(G, 0, 6 * ms * sizeof(T), st) != cudaSuccess) return launch_ok(), TRID_ERR_CUDA;
+    if (cudaMemsetAsync(gwb[0], 0, ms * sizeof(T), st) != cudaSuccess ||
+        cudaMemsetAsync(gdb[0], 0, ms * sizeof(T), st) != cudaSuccess)
+        return launch_ok(), TRID_ERR_CUDA;
     if (cudaMemcpyAsync(g, guT, n * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return launch_ok(), TRID_ERR_CUDA;
     const int nseg = l.nseg;
+    int cur = 0;  // which g_w / g_d buffers this step uses (zeroed)
     for (int seg = nseg - 1; seg >= 0 && nsteps > 0; --seg) {
         const int t0 = seg * K;
         const int t1 = (t0 + K < nsteps) ? t0 + K : nsteps;
@@ -297,26 +365,30 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
                             st) != cudaSuccess)
             return launch_ok(), TRID_ERR_CUDA;
         for (int q = 0; q < L; ++q) {
-            T *un = (q + 1 < L) ? U + size_t(q + 1) * ms : nullptr;
-            const trid_status s = v2_forward_step<T>(U + size_t(q) * ms, gd, co, dims, scr,
-                                                     l.scratch, dt, st, W + size_t(q) * ms,
-                                                     D + size_t(q) * ms, un);
+            const T *up = q > 0 ? U + size_t(q - 1) * ms : nullptr;
+            const T *dp = q > 0 ? D + size_t(q - 1) * ms : nullptr;
+            const trid_status s = v2_recompute_step<T>(up, dp, U + size_t(q) * ms,
+                                                       W + size_t(q) * ms, D + size_t(q) * ms, co,
+                                                       dims, scr, l.scratch, dt, st);
             if (s != TRID_OK) return s;
         }
         for (int q = L - 1; q >= 0; --q) {
-            trid_status s = trid_solve_batch_adjoint(co[3], co[4], co[5], D + size_t(q) * ms, g,
-                                                     sg + 3 * ms, sg + 4 * ms, sg + 5 * ms, gw,
-                                                     dims, 2, 1, dt, scr, l.scratch, st);
+            T *gw = gwb[cur], *gd = gdb[cur];
+            // g_w = Y^{-T} g, g_d = X^{-T} g_w: accumulated into the zeroed buffers
+            trid_status s = trid_solve_batch_ws(tr + 2 * ms, co[4], tr + 3 * ms, g, gw, dims, 2,
+                                                1, dt, scr, l.scratch, st);
             if (s != TRID_OK) return s;
-            s = trid_solve_batch_adjoint(co[0], co[1], co[2], W + size_t(q) * ms, gw, sg, sg + ms,
-                                         sg + 2 * ms, gd, dims, 2, 0, dt, scr, l.scratch, st);
+            s = trid_solve_batch_ws(tr, co[1], tr + ms, gw, gd, dims, 2, 0, dt, scr, l.scratch,
+                                    st);
             if (s != TRID_OK) return s;
-            k_v2_rhs_adj<T><<<g2, b2, 0, st>>>(g, gd, U + size_t(q) * ms, co[0], co[2], co[3],
-                                                co[5], sg, G, gn, nx, ny, ms);
+            k_v2_rhs_adj<T><<<g2, b2, 0, st>>>(g, gd, gw, U + size_t(q) * ms, W + size_t(q) * ms,
+                                                D + size_t(q) * ms, co[0], co[2], co[3], co[5], G,
+                                                gn, gdb[cur ^ 1], gwb[cur ^ 1], nx, ny, ms);
             if (!launch_ok()) return TRID_ERR_CUDA;
             T *tmp = g;
             g = gn;
             gn = tmp;
+            cur ^= 1;
         }
     }
     if (cudaMemcpyAsync(gu0, g, n * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
