@@ -125,13 +125,18 @@ __global__ void k_v2_rhs_keep(const T *__restrict__ up, const T *__restrict__ dp
 }
 
 // Reverse of the explicit part and of the identity path, plus the summed
-// coefficient gradients:  gn = g + S^T gm  (gm = g_d on the interior),
-// G_k += (gradient of coefficient k through the two solves) + stencil term.
+// coefficient gradients:  gn = g + S^T gm  (gm = g_d on the interior).
 // Gather form: point q collects the stencil rows p = q, q +- 1, q +- nx that
 // read u_q.  w and dl are the step's X^{-1} d and delta; gd_next and gw_next
 // (the other buffers of the pair) are zeroed for the next step's accumulating
-// adjoint solves.
-template <typename T>
+// adjoint solves.  Per point p the step's coefficient gradients are
+//   a_x: -g_d,p w_{p-1} + gm_p (u_p - u_{p-1}),  b_x: -g_d,p w_p,
+//   c_x: -g_d,p w_{p+1} + gm_p (u_p - u_{p+1})   (y alike with g_w, delta).
+// COEF: G_k += each of the six (the caller wants them); otherwise only the
+// face sums that the kappa gradient needs are kept: F_x[p] += (b_x - a_x) at
+// p + 1 (if interior) + (b_x - c_x) at p (if interior), face (p, p + 1);
+// F_y alike for face (p, p + nx).
+template <typename T, bool COEF>
 __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
                              const T *__restrict__ gw, const T *__restrict__ u,
                              const T *__restrict__ w, const T *__restrict__ dl,
@@ -139,7 +144,7 @@ __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
                              const T *__restrict__ ay, const T *__restrict__ cy, T *__restrict__ G,
                              T *__restrict__ gn, T *__restrict__ gd_next, T *__restrict__ gw_next,
                              int nx, int ny, size_t n) {
-    // n: element stride between the six arrays of G
+    // n: element stride between the arrays of G
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= nx) continue;
@@ -155,30 +160,76 @@ __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
         if (j > 0) acc -= cy[p - nx] * gm(i, j - 1);
         if (j < ny - 1) acc -= ay[p + nx] * gm(i, j + 1);
         gn[p] = acc;
-        // coefficient gradients of the x solve (w = X^{-1} d) and of the y
-        // solve (delta = Y^{-1} w), then the stencil's terms
-        const T gdp = gd[p], gwp = gw[p];
-        T sa = i > 0 ? -gdp * w[p - 1] : T(0);
-        const T sb = -gdp * w[p];
-        T sc = i < nx - 1 ? -gdp * w[p + 1] : T(0);
-        T ta = j > 0 ? -gwp * dl[p - nx] : T(0);
-        const T tb = -gwp * dl[p];
-        T tc = j < ny - 1 ? -gwp * dl[p + nx] : T(0);
-        const T uc = u[p];
-        if (g0 != T(0)) {
-            sa += g0 * (uc - u[p - 1]);
-            sc += g0 * (uc - u[p + 1]);
-            ta += g0 * (uc - u[p - nx]);
-            tc += g0 * (uc - u[p + nx]);
+        // the step's coefficient gradients at point q = (ii, jj)
+        auto xgrad = [&](int ii, size_t q, T &sa, T &sb, T &sc) {
+            const T gdq = gd[q], gq = gm(ii, j), uq = u[q];
+            sa = ii > 0 ? -gdq * w[q - 1] : T(0);
+            sb = -gdq * w[q];
+            sc = ii < nx - 1 ? -gdq * w[q + 1] : T(0);
+            if (gq != T(0)) {
+                sa += gq * (uq - u[q - 1]);
+                sc += gq * (uq - u[q + 1]);
+            }
+        };
+        auto ygrad = [&](int jj, size_t q, T &ta, T &tb, T &tc) {
+            const T gwq = gw[q], gq = gm(i, jj), uq = u[q];
+            ta = jj > 0 ? -gwq * dl[q - nx] : T(0);
+            tb = -gwq * dl[q];
+            tc = jj < ny - 1 ? -gwq * dl[q + nx] : T(0);
+            if (gq != T(0)) {
+                ta += gq * (uq - u[q - nx]);
+                tc += gq * (uq - u[q + nx]);
+            }
+        };
+        T sa, sb, sc, ta, tb, tc;
+        xgrad(i, p, sa, sb, sc);
+        ygrad(j, p, ta, tb, tc);
+        if (COEF) {
+            G[p] += sa;
+            G[n + p] += sb;
+            G[2 * n + p] += sc;
+            G[3 * n + p] += ta;
+            G[4 * n + p] += tb;
+            G[5 * n + p] += tc;
+        } else {
+            if (i < nx - 1) {  // face (p, p + 1)
+                T f = (i > 0) ? sb - sc : T(0);
+                if (i + 1 < nx - 1) {
+                    T a1, b1, c1;
+                    xgrad(i + 1, p + 1, a1, b1, c1);
+                    f += b1 - a1;
+                }
+                G[p] += f;
+            }
+            if (j < ny - 1) {  // face (p, p + nx)
+                T f = (j > 0) ? tb - tc : T(0);
+                if (j + 1 < ny - 1) {
+                    T a1, b1, c1;
+                    ygrad(j + 1, p + nx, a1, b1, c1);
+                    f += b1 - a1;
+                }
+                G[n + p] += f;
+            }
         }
-        G[p] += sa;
-        G[n + p] += sb;
-        G[2 * n + p] += sc;
-        G[3 * n + p] += ta;
-        G[4 * n + p] += tb;
-        G[5 * n + p] += tc;
         gd_next[p] = T(0);
         gw_next[p] = T(0);
+    }
+}
+
+// Face sums -> kappa: node p takes half of each of its faces' gradients.
+template <typename T>
+__global__ void k_v2_kappa_faces(const T *__restrict__ F, T *__restrict__ gk, int nx, int ny,
+                                 T lam, size_t n) {
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= nx) continue;
+        const size_t p = size_t(j) * nx + i;
+        T v = T(0);
+        if (i > 0) v += T(0.5) * (lam * F[p - 1]);
+        if (i < nx - 1) v += T(0.5) * (lam * F[p]);
+        if (j > 0) v += T(0.5) * (lam * F[n + p - nx]);
+        if (j < ny - 1) v += T(0.5) * (lam * F[n + p]);
+        gk[p] = v;
     }
 }
 
@@ -349,7 +400,9 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     k_v2_transpose<T><<<g2, b2, 0, st>>>(co[0], co[2], co[3], co[5], tr, tr + ms, tr + 2 * ms,
                                          tr + 3 * ms, nx, ny);
     if (!launch_ok()) return TRID_ERR_CUDA;
-    if (cudaMemsetAsync(G, 0, 6 * ms * sizeof(T), st) != cudaSuccess) return launch_ok(), TRID_ERR_CUDA;
+    // the six coefficient-gradient sums, or (no g_coef wanted) the two face sums
+    if (cudaMemsetAsync(G, 0, (gcoef ? 6 : 2) * ms * sizeof(T), st) != cudaSuccess)
+        return launch_ok(), TRID_ERR_CUDA;
     if (cudaMemsetAsync(gwb[0], 0, ms * sizeof(T), st) != cudaSuccess ||
         cudaMemsetAsync(gdb[0], 0, ms * sizeof(T), st) != cudaSuccess)
         return launch_ok(), TRID_ERR_CUDA;
@@ -381,9 +434,10 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
             s = trid_solve_batch_ws(tr, co[1], tr + ms, gw, gd, dims, 2, 0, dt, scr, l.scratch,
                                     st);
             if (s != TRID_OK) return s;
-            k_v2_rhs_adj<T><<<g2, b2, 0, st>>>(g, gd, gw, U + size_t(q) * ms, W + size_t(q) * ms,
-                                                D + size_t(q) * ms, co[0], co[2], co[3], co[5], G,
-                                                gn, gdb[cur ^ 1], gwb[cur ^ 1], nx, ny, ms);
+            auto kern = gcoef ? k_v2_rhs_adj<T, true> : k_v2_rhs_adj<T, false>;
+            kern<<<g2, b2, 0, st>>>(g, gd, gw, U + size_t(q) * ms, W + size_t(q) * ms,
+                                    D + size_t(q) * ms, co[0], co[2], co[3], co[5], G, gn,
+                                    gdb[cur ^ 1], gwb[cur ^ 1], nx, ny, ms);
             if (!launch_ok()) return TRID_ERR_CUDA;
             T *tmp = g;
             g = gn;
@@ -393,7 +447,10 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     }
     if (cudaMemcpyAsync(gu0, g, n * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return launch_ok(), TRID_ERR_CUDA;
-    k_v2_kappa<T><<<g2, b2, 0, st>>>(G, gk, nx, ny, lam, ms);
+    if (gcoef)
+        k_v2_kappa<T><<<g2, b2, 0, st>>>(G, gk, nx, ny, lam, ms);
+    else
+        k_v2_kappa_faces<T><<<g2, b2, 0, st>>>(G, gk, nx, ny, lam, ms);
     if (!launch_ok()) return TRID_ERR_CUDA;
     if (gcoef) {
         for (int k = 0; k < 6; ++k)

@@ -35,13 +35,17 @@ def dev(x, dtype):
     return torch.from_numpy(np.ascontiguousarray(x.astype(dtype))).cuda()
 
 
-def gpu_run(u0, kap, tg, dims, lam, steps, every, dtype):
+def gpu_run(u0, kap, tg, dims, lam, steps, every, dtype, want_coef=False):
+    """Forward and backward on the GPU.  Without want_coef the backward keeps
+    only the face sums that the kappa gradient needs; with it, the six summed
+    coefficient gradients too (returned last, else None)."""
     tu, tk, tt = (dev(v, dtype) for v in (u0, kap, tg))
     uT, ck = trid.adi2v_forward(tu, tk, dims, lam, steps, every)
     g = 2.0 * (uT - tt) / tu.numel()
-    gu, gk, gc = trid.adi2v_backward(g, tk, dims, lam, steps, every, ck, want_coef=True)
+    gu, gk, gc = trid.adi2v_backward(g, tk, dims, lam, steps, every, ck, want_coef=want_coef)
     torch.cuda.synchronize()
-    return uT.cpu().numpy(), gu.cpu().numpy(), gk.cpu().numpy(), gc.cpu().numpy()
+    return (uT.cpu().numpy(), gu.cpu().numpy(), gk.cpu().numpy(),
+            gc.cpu().numpy() if gc is not None else None)
 
 
 CASES = [((33, 20), 0.3, 5, 2), ((64, 48), 0.2, 12, 5), ((300, 40), 0.25, 4, 3),
@@ -53,13 +57,16 @@ CASES = [((33, 20), 0.3, 5, 2), ((64, 48), 0.2, 12, 5), ((300, 40), 0.25, 4, 3),
                          ids=[f"{d[0]}x{d[1]}-{s}steps-every{e}" for d, _, s, e in CASES])
 def test_forward_and_gradient_vs_oracle(dims, lam, steps, every, dtype):
     u0, kap, tg = problem(dims, sum(dims), dtype)
-    uT, gu, gk, gc = gpu_run(u0, kap, tg, dims, lam, steps, every, dtype)
     ref_uT = oracle.adi2v(u0, kap, dims, lam, steps)
     loss, rgu, rgk, rgc = oracle.adi2v_grad(u0, kap, tg, dims, lam, steps)
-    assert normwise(uT, ref_uT) <= TOL_FWD[dtype]
-    assert normwise(gu, rgu) <= TOL_GRAD[dtype]
-    assert normwise(gk, rgk) <= TOL_GRAD[dtype]
-    assert normwise(gc, rgc) <= TOL_GRAD[dtype]
+    # both forms of the backward: face sums only, and all six coefficient gradients
+    for want in (False, True):
+        uT, gu, gk, gc = gpu_run(u0, kap, tg, dims, lam, steps, every, dtype, want_coef=want)
+        assert normwise(uT, ref_uT) <= TOL_FWD[dtype]
+        assert normwise(gu, rgu) <= TOL_GRAD[dtype]
+        assert normwise(gk, rgk) <= TOL_GRAD[dtype]
+        if want:
+            assert normwise(gc, rgc) <= TOL_GRAD[dtype]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
@@ -68,14 +75,16 @@ def test_checkpoint_spacing_does_not_change_the_gradient(dtype):
     states exactly, so every spacing gives the same bits."""
     dims, lam, steps = (96, 40), 0.2, 12
     u0, kap, tg = problem(dims, 5, dtype)
-    ref = None
-    for every in (1, 5, 12, 40):
-        _, gu, gk, gc = gpu_run(u0, kap, tg, dims, lam, steps, every, dtype)
-        if ref is None:
-            ref = (gu, gk, gc)
-        else:
-            for a, b in zip((gu, gk, gc), ref):
-                assert np.array_equal(a, b)
+    for want in (False, True):
+        ref = None
+        for every in (1, 5, 12, 40):
+            _, gu, gk, gc = gpu_run(u0, kap, tg, dims, lam, steps, every, dtype, want_coef=want)
+            got = (gu, gk, gc) if want else (gu, gk)
+            if ref is None:
+                ref = got
+            else:
+                for a, b in zip(got, ref):
+                    assert np.array_equal(a, b)
 
 
 def test_autograd_matches_direct_calls():

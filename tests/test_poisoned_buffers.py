@@ -131,7 +131,11 @@ def test_adi2v_outputs_workspace_and_checkpoints_poisoned(lib, dt):
     trid.adi2v_forward(u0, kap, dims, lam, steps, every, uT=uT2, ckpt=ck2, workspace=nan_bytes(wsb))
     gu2, gk2, gc2 = trid.adi2v_backward(g, kap, dims, lam, steps, every, ck2, want_coef=True,
                                         workspace=nan_bytes(wsb))
+    # and the form that keeps only the face sums of the coefficient gradients
+    gu3, gk3, _ = trid.adi2v_backward(g, kap, dims, lam, steps, every, ck)
+    gu4, gk4, _ = trid.adi2v_backward(g, kap, dims, lam, steps, every, ck2,
+                                      workspace=nan_bytes(wsb))
     torch.cuda.synchronize()
     assert torch.equal(uT2, uT)
-    for got, want in ((gu2, gu), (gk2, gk), (gc2, gc)):
+    for got, want in ((gu2, gu), (gk2, gk), (gc2, gc), (gu4, gu3), (gk4, gk3)):
         assert torch.equal(got, want)
