@@ -136,54 +136,63 @@ __global__ void k_v2_rhs_keep(const T *__restrict__ up, const T *__restrict__ dp
 // face sums that the kappa gradient needs are kept: F_x[p] += (b_x - a_x) at
 // p + 1 (if interior) + (b_x - c_x) at p (if interior), face (p, p + 1);
 // F_y alike for face (p, p + nx).
+//
+// Each thread walks V2_ROWS consecutive rows of one column, keeping the
+// column's values of the rows above and below in registers (the x
+// neighbours are read directly and mostly hit L1).
+constexpr int V2_ROWS = 8;
+
 template <typename T, bool COEF>
-__global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
-                             const T *__restrict__ gw, const T *__restrict__ u,
-                             const T *__restrict__ w, const T *__restrict__ dl,
-                             const T *__restrict__ ax, const T *__restrict__ cx,
-                             const T *__restrict__ ay, const T *__restrict__ cy, T *__restrict__ G,
-                             T *__restrict__ gn, T *__restrict__ gd_next, T *__restrict__ gw_next,
-                             int nx, int ny, size_t n) {
+__global__ void __launch_bounds__(256)
+k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd, const T *__restrict__ gw,
+             const T *__restrict__ u, const T *__restrict__ w, const T *__restrict__ dl,
+             const T *__restrict__ ax, const T *__restrict__ cx, const T *__restrict__ ay,
+             const T *__restrict__ cy, T *__restrict__ G, T *__restrict__ gn,
+             T *__restrict__ gd_next, T *__restrict__ gw_next, int nx, int ny, size_t n) {
     // n: element stride between the arrays of G
-    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= nx) continue;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const bool xin = i > 0 && i < nx - 1;
+    for (int64_t jb = int64_t(blockIdx.y) * V2_ROWS; jb < ny; jb += int64_t(gridDim.y) * V2_ROWS) {
+    const int j0 = int(jb);
+    const int j1 = j0 + V2_ROWS < ny ? j0 + V2_ROWS : ny;
+    auto col = [&](const T *a, int jj) -> T {  // a at (i, jj), 0 outside the mesh
+        return (jj >= 0 && jj < ny) ? a[size_t(jj) * nx + i] : T(0);
+    };
+    auto mask = [&](int jj, T v) -> T { return (xin && jj > 0 && jj < ny - 1) ? v : T(0); };
+    // column window: rows j - 1, j, j + 1 (u, delta, g_d), j, j + 1 (g_w, a_y),
+    // j - 1, j (c_y)
+    T u_m = col(u, j0 - 1), u_c = col(u, j0), u_p = col(u, j0 + 1);
+    T d_m = col(dl, j0 - 1), d_c = col(dl, j0), d_p = col(dl, j0 + 1);
+    T r_m = col(gd, j0 - 1), r_c = col(gd, j0), r_p = col(gd, j0 + 1);
+    T gw_c = col(gw, j0), gw_p = col(gw, j0 + 1);
+    T ay_c = col(ay, j0), ay_p = col(ay, j0 + 1);
+    T cy_m = col(cy, j0 - 1), cy_c = col(cy, j0);
+    for (int j = j0; j < j1; ++j) {
         const size_t p = size_t(j) * nx + i;
-        auto gm = [&](int ii, int jj) -> T {
-            return (ii > 0 && ii < nx - 1 && jj > 0 && jj < ny - 1) ? gd[size_t(jj) * nx + ii]
-                                                                     : T(0);
+        auto gmx = [&](int ii) -> T {  // g_d on the interior at (ii, j)
+            return (ii > 0 && ii < nx - 1 && j > 0 && j < ny - 1) ? gd[p + (ii - i)] : T(0);
         };
-        const T g0 = gm(i, j);
-        T acc = g[p] + (ax[p] + cx[p] + ay[p] + cy[p]) * g0;
-        if (i > 0) acc -= cx[p - 1] * gm(i - 1, j);
-        if (i < nx - 1) acc -= ax[p + 1] * gm(i + 1, j);
-        if (j > 0) acc -= cy[p - nx] * gm(i, j - 1);
-        if (j < ny - 1) acc -= ay[p + nx] * gm(i, j + 1);
+        const T g0 = mask(j, r_c);
+        T acc = g[p] + (ax[p] + cx[p] + ay_c + cy_c) * g0;
+        if (i > 0) acc -= cx[p - 1] * gmx(i - 1);
+        if (i < nx - 1) acc -= ax[p + 1] * gmx(i + 1);
+        if (j > 0) acc -= cy_m * mask(j - 1, r_m);
+        if (j < ny - 1) acc -= ay_p * mask(j + 1, r_p);
         gn[p] = acc;
-        // the step's coefficient gradients at point q = (ii, jj)
-        auto xgrad = [&](int ii, size_t q, T &sa, T &sb, T &sc) {
-            const T gdq = gd[q], gq = gm(ii, j), uq = u[q];
-            sa = ii > 0 ? -gdq * w[q - 1] : T(0);
-            sb = -gdq * w[q];
-            sc = ii < nx - 1 ? -gdq * w[q + 1] : T(0);
-            if (gq != T(0)) {
-                sa += gq * (uq - u[q - 1]);
-                sc += gq * (uq - u[q + 1]);
-            }
-        };
-        auto ygrad = [&](int jj, size_t q, T &ta, T &tb, T &tc) {
-            const T gwq = gw[q], gq = gm(i, jj), uq = u[q];
-            ta = jj > 0 ? -gwq * dl[q - nx] : T(0);
-            tb = -gwq * dl[q];
-            tc = jj < ny - 1 ? -gwq * dl[q + nx] : T(0);
-            if (gq != T(0)) {
-                ta += gq * (uq - u[q - nx]);
-                tc += gq * (uq - u[q + nx]);
-            }
-        };
-        T sa, sb, sc, ta, tb, tc;
-        xgrad(i, p, sa, sb, sc);
-        ygrad(j, p, ta, tb, tc);
+        // the step's coefficient gradients at p: x solve and stencil, y solve and stencil
+        T sa = i > 0 ? -r_c * w[p - 1] : T(0);
+        const T sb = -r_c * w[p];
+        T sc = i < nx - 1 ? -r_c * w[p + 1] : T(0);
+        T ta = j > 0 ? -gw_c * d_m : T(0);
+        const T tb = -gw_c * d_c;
+        T tc = j < ny - 1 ? -gw_c * d_p : T(0);
+        if (g0 != T(0)) {
+            sa += g0 * (u_c - u[p - 1]);
+            sc += g0 * (u_c - u[p + 1]);
+            ta += g0 * (u_c - u_m);
+            tc += g0 * (u_c - u_p);
+        }
         if (COEF) {
             G[p] += sa;
             G[n + p] += sb;
@@ -192,11 +201,13 @@ __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
             G[4 * n + p] += tb;
             G[5 * n + p] += tc;
         } else {
-            if (i < nx - 1) {  // face (p, p + 1)
+            if (i < nx - 1) {  // face (p, p + 1): (b - c) at p, (b - a) at p + 1
                 T f = (i > 0) ? sb - sc : T(0);
                 if (i + 1 < nx - 1) {
-                    T a1, b1, c1;
-                    xgrad(i + 1, p + 1, a1, b1, c1);
+                    const T r1 = gd[p + 1], g1 = gmx(i + 1), u1 = u[p + 1];
+                    T a1 = -r1 * w[p];
+                    const T b1 = -r1 * w[p + 1];
+                    if (g1 != T(0)) a1 += g1 * (u1 - u_c);
                     f += b1 - a1;
                 }
                 G[p] += f;
@@ -204,8 +215,10 @@ __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
             if (j < ny - 1) {  // face (p, p + nx)
                 T f = (j > 0) ? tb - tc : T(0);
                 if (j + 1 < ny - 1) {
-                    T a1, b1, c1;
-                    ygrad(j + 1, p + nx, a1, b1, c1);
+                    const T g1 = mask(j + 1, r_p);
+                    T a1 = -gw_p * d_c;
+                    const T b1 = -gw_p * d_p;
+                    if (g1 != T(0)) a1 += g1 * (u_p - u_c);
                     f += b1 - a1;
                 }
                 G[n + p] += f;
@@ -213,6 +226,14 @@ __global__ void k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd,
         }
         gd_next[p] = T(0);
         gw_next[p] = T(0);
+        // slide the column window down one row
+        u_m = u_c; u_c = u_p; u_p = col(u, j + 2);
+        d_m = d_c; d_c = d_p; d_p = col(dl, j + 2);
+        r_m = r_c; r_c = r_p; r_p = col(gd, j + 2);
+        gw_c = gw_p; gw_p = col(gw, j + 2);
+        ay_c = ay_p; ay_p = col(ay, j + 2);
+        cy_m = cy_c; cy_c = col(cy, j + 1);
+    }
     }
 }
 
@@ -396,6 +417,9 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     char *scr = ws + (6 + 4 + 3 * size_t(K) + 2 + 4 + 6) * l.mesh;
     dim3 g2, b2;
     grid2<T>(nx, ny, g2, b2);
+    // the column-walking reverse kernel: V2_ROWS rows per thread
+    const int64_t bands = (int64_t(ny) + V2_ROWS - 1) / V2_ROWS;
+    const dim3 ga(unsigned((nx + 255) / 256), unsigned(bands < 65535 ? bands : 65535));
     k_v2_coef<T><<<g2, b2, 0, st>>>(kap, co[0], co[1], co[2], co[3], co[4], co[5], nx, ny, lam);
     k_v2_transpose<T><<<g2, b2, 0, st>>>(co[0], co[2], co[3], co[5], tr, tr + ms, tr + 2 * ms,
                                          tr + 3 * ms, nx, ny);
@@ -435,7 +459,7 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
                                     st);
             if (s != TRID_OK) return s;
             auto kern = gcoef ? k_v2_rhs_adj<T, true> : k_v2_rhs_adj<T, false>;
-            kern<<<g2, b2, 0, st>>>(g, gd, gw, U + size_t(q) * ms, W + size_t(q) * ms,
+            kern<<<ga, b2, 0, st>>>(g, gd, gw, U + size_t(q) * ms, W + size_t(q) * ms,
                                     D + size_t(q) * ms, co[0], co[2], co[3], co[5], G, gn,
                                     gdb[cur ^ 1], gwb[cur ^ 1], nx, ny, ms);
             if (!launch_ok()) return TRID_ERR_CUDA;
