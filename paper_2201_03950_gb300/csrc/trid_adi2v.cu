@@ -34,6 +34,7 @@
 
 #include "../../include/trid.h"
 #include "trid_internal.h"
+#include "trid_tma.cuh"
 
 namespace trid {
 
@@ -62,11 +63,16 @@ __global__ void k_v2_coef(const T *__restrict__ kap, T *ax, T *bx, T *cx, T *ay,
     }
 }
 
+// The per-step kernels are launched with programmatic dependent launch (the
+// next kernel may be scheduled while the previous one drains); each waits
+// for the previous kernel before touching memory, and their pointers are not
+// __restrict__, so that no load is moved ahead of that wait.
+//
 // Explicit part: d = lam (Lx + Ly) u on the interior, 0 on the boundary.
 template <typename T>
-__global__ void k_v2_rhs(const T *__restrict__ u, const T *__restrict__ ax,
-                         const T *__restrict__ cx, const T *__restrict__ ay,
-                         const T *__restrict__ cy, T *__restrict__ d, int nx, int ny) {
+__global__ void k_v2_rhs(const T *u, const T *ax, const T *cx, const T *ay, const T *cy, T *d,
+                         int nx, int ny) {
+    pdl_wait();
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= nx) continue;
@@ -103,10 +109,9 @@ __global__ void k_v2_transpose(const T *__restrict__ ax, const T *__restrict__ c
 // u; d = lam (Lx + Ly) u as k_v2_rhs; dz zeroed (the step's delta, which the
 // y solve then accumulates into).
 template <typename T>
-__global__ void k_v2_rhs_keep(const T *__restrict__ up, const T *__restrict__ dp, T *u,
-                              const T *__restrict__ ax, const T *__restrict__ cx,
-                              const T *__restrict__ ay, const T *__restrict__ cy,
-                              T *__restrict__ d, T *__restrict__ dz, int nx, int ny) {
+__global__ void k_v2_rhs_keep(const T *up, const T *dp, T *u, const T *ax, const T *cx,
+                              const T *ay, const T *cy, T *d, T *dz, int nx, int ny) {
+    pdl_wait();
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= nx) continue;
@@ -144,11 +149,10 @@ constexpr int V2_ROWS = 8;
 
 template <typename T, bool COEF>
 __global__ void __launch_bounds__(256)
-k_v2_rhs_adj(const T *__restrict__ g, const T *__restrict__ gd, const T *__restrict__ gw,
-             const T *__restrict__ u, const T *__restrict__ w, const T *__restrict__ dl,
-             const T *__restrict__ ax, const T *__restrict__ cx, const T *__restrict__ ay,
-             const T *__restrict__ cy, T *__restrict__ G, T *__restrict__ gn,
-             T *__restrict__ gd_next, T *__restrict__ gw_next, int nx, int ny, size_t n) {
+k_v2_rhs_adj(const T *g, const T *gd, const T *gw, const T *u, const T *w, const T *dl,
+             const T *ax, const T *cx, const T *ay, const T *cy, T *G, T *gn, T *gd_next,
+             T *gw_next, int nx, int ny, size_t n) {
+    pdl_wait();
     // n: element stride between the arrays of G
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx) return;
@@ -321,6 +325,29 @@ static bool v2_layout(const int64_t *dims, int nsteps, int every, trid_dtype dty
     return true;
 }
 
+// Launch with programmatic dependent launch allowed.
+template <typename... KArgs, typename... Args>
+static bool launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 template <typename T>
 static void grid2(int nx, int ny, dim3 &g, dim3 &b) {
     b = dim3(256);
@@ -333,8 +360,8 @@ static trid_status v2_forward_step(T *u, T *dw, const T *const co[6], const int6
     const int nx = int(dims[0]), ny = int(dims[1]);
     dim3 g, b;
     grid2<T>(nx, ny, g, b);
-    k_v2_rhs<T><<<g, b, 0, st>>>(u, co[0], co[2], co[3], co[5], dw, nx, ny);
-    if (!launch_ok()) return TRID_ERR_CUDA;
+    if (!launch_pdl(k_v2_rhs<T>, g, b, st, u, co[0], co[2], co[3], co[5], dw, nx, ny))
+        return TRID_ERR_CUDA;
     trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], dw, nullptr, dims, 2, 0, dt, scr,
                                         scr_bytes, st);
     if (s != TRID_OK) return s;
@@ -355,8 +382,9 @@ static trid_status v2_recompute_step(const T *up, const T *dp, T *u, T *w, T *dl
     const int nx = int(dims[0]), ny = int(dims[1]);
     dim3 g, b;
     grid2<T>(nx, ny, g, b);
-    k_v2_rhs_keep<T><<<g, b, 0, st>>>(up, dp, u, co[0], co[2], co[3], co[5], w, dl, nx, ny);
-    if (!launch_ok()) return TRID_ERR_CUDA;
+    if (!launch_pdl(k_v2_rhs_keep<T>, g, b, st, up, dp, u, co[0], co[2], co[3], co[5], w, dl, nx,
+                    ny))
+        return TRID_ERR_CUDA;
     trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], w, nullptr, dims, 2, 0, dt, scr,
                                         scr_bytes, st);
     if (s != TRID_OK) return s;
@@ -459,10 +487,10 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
                                     st);
             if (s != TRID_OK) return s;
             auto kern = gcoef ? k_v2_rhs_adj<T, true> : k_v2_rhs_adj<T, false>;
-            kern<<<ga, b2, 0, st>>>(g, gd, gw, U + size_t(q) * ms, W + size_t(q) * ms,
-                                    D + size_t(q) * ms, co[0], co[2], co[3], co[5], G, gn,
-                                    gdb[cur ^ 1], gwb[cur ^ 1], nx, ny, ms);
-            if (!launch_ok()) return TRID_ERR_CUDA;
+            if (!launch_pdl(kern, ga, b2, st, g, gd, gw, U + size_t(q) * ms, W + size_t(q) * ms,
+                            D + size_t(q) * ms, co[0], co[2], co[3], co[5], G, gn, gdb[cur ^ 1],
+                            gwb[cur ^ 1], nx, ny, ms))
+                return TRID_ERR_CUDA;
             T *tmp = g;
             g = gn;
             gn = tmp;

@@ -78,18 +78,6 @@ struct WinSplit {
     float Wt[4][WIN_H], Wb[4][WIN_H];
 };
 
-// Programmatic dependent launch: the next kernel on the stream may be
-// scheduled once every CTA of this one has started; each kernel waits for the
-// previous one to complete (and its memory to be visible) before touching
-// data that kernel produced or reads.  Pointers to such data are not
-// __restrict__: the compiler may otherwise treat them as unchanging for the
-// whole kernel and read them through the non-coherent path or ahead of the
-// wait.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // Fold factors of the x solve per lane kind (0 first tile of the line,
 // 1 interior tile, 2 last tile, 3 lane beyond the line); the reduced rows of
 // the constant operator are the same for every interior tile.

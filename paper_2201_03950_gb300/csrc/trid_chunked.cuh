@@ -128,6 +128,9 @@ k_chunk_cluster(const __grid_constant__ TmaSet maps, T *out, int accumulate, Lin
     namespace cg = cooperative_groups;
     constexpr int NT = CK_NT, SG = CK_SG, M = CM, CH = CK_NT * CM;
     static_assert(CH % CK_BOX == 0, "a chunk is whole TMA boxes");
+    // programmatic dependent launch (one wave of clusters): see k_lines_tma
+    pdl_trigger();
+    pdl_wait();
     using LY = ChunkLayout<T, CM>;
     constexpr int P = LY::P;
     extern __shared__ __align__(128) unsigned char smem[];

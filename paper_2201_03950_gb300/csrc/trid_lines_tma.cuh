@@ -131,9 +131,13 @@ struct LinesTmaLayout {
 // banks (the plain layout gives a 2- or 4-way conflict at that lane stride).
 template <typename T, int TW, int M, int SPS, bool SWZ>
 __global__ void __launch_bounds__(LT_CONS + 32, 1)
-k_lines_tma(const __grid_constant__ TmaSet maps, const T *__restrict__ a,
-            const T *__restrict__ b, const T *__restrict__ c, const T *d, T *out,
-            int accumulate, int nsys, int n, int nbatch, int stages, int *status) {
+k_lines_tma(const __grid_constant__ TmaSet maps, const T *a, const T *b, const T *c, const T *d,
+            T *out, int accumulate, int nsys, int n, int nbatch, int stages, int *status) {
+    // launched with programmatic dependent launch: one wave of persistent
+    // blocks, so the next kernel may be scheduled at once; nothing is read or
+    // written before the previous kernel has completed
+    pdl_trigger();
+    pdl_wait();
     static_assert(!SWZ || M * sizeof(T) == 32 || M * sizeof(T) == 64,
                   "swizzled rows are 32 or 64 bytes");
     using LY = LinesTmaLayout<T, TW, SPS>;

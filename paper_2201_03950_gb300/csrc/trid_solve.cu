@@ -334,10 +334,24 @@ static bool launch_lines_tma_tw(const float *a, const float *b, const float *c, 
     const int64_t nbatch = (L.nsys + SPS - 1) / SPS;
     const int64_t slots = int64_t(di->sm_count) * per_sm;
     const int64_t grid = nbatch < slots ? nbatch : slots;
-    kern<<<dim3(unsigned(grid)), LT_CONS + 32, smem, st>>>(maps, a, b, c, d, out, acc,
-                                                           int(L.nsys), n, int(nbatch), stages,
-                                                           device_status_word());
-    return cudaGetLastError() == cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(LT_CONS + 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, a, b, c, d, out, acc, int(L.nsys),
+                                             n, int(nbatch), stages, device_status_word());
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        cudaGetLastError();
+        return false;
+    }
+    return true;
 }
 
 template <typename T>
@@ -400,17 +414,19 @@ static bool launch_chunk_cluster_cm(const T *a, const T *b, const T *c, const T 
     if (ncl_max < 1) return false;
     const int64_t ncl = nstrips < ncl_max ? nstrips : ncl_max;
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = unsigned(C);
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3(unsigned(C * ncl));
     cfg.blockDim = dim3(CK_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, out, acc, L, int(nstrips),
                                              tma_store, device_status_word());
     if (e != cudaSuccess) {

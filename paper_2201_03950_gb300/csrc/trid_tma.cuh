@@ -76,6 +76,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *s
     return true;
 }
 
+// Programmatic dependent launch: the next kernel on the stream may be
+// scheduled once every CTA of this one has started; each kernel waits for the
+// previous one to complete (and its memory to be visible) before touching
+// data that kernel produced or reads.  Pointers to such data are not
+// __restrict__: the compiler may otherwise treat them as unchanging for the
+// whole kernel and read them through the non-coherent path or ahead of the
+// wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Address of the same shared-memory location in CTA `rank` of the cluster.
 __device__ __forceinline__ uint32_t cluster_map(uint32_t saddr, uint32_t rank) {
     uint32_t r;
