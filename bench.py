@@ -398,7 +398,7 @@ def run_ours(args):
             gf, gbk = bf / (mf * 1e-3) / 1e9, bb / (mb * 1e-3) / 1e9
             gtot = (bf + bb) / ((mf + mb) * 1e-3) / 1e9
             # the same forward + backward captured once in a CUDA graph and
-            # replayed (about 30 launches per step go to the graph)
+            # replayed (about 6 launches per step and direction go to the graph)
             gv2 = 2.0 * (uTv - tv) / nv
             gvg = torch.cuda.CUDAGraph()
             with torch.cuda.graph(gvg):

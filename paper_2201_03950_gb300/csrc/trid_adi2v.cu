@@ -325,7 +325,7 @@ static bool v2_layout(const int64_t *dims, int nsteps, int every, trid_dtype dty
     return true;
 }
 
-// Launch with programmatic dependent launch allowed.
+// Launch with programmatic dependent launch allowed (outside stream capture).
 template <typename... KArgs, typename... Args>
 static bool launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
                        Args... args) {
@@ -338,7 +338,7 @@ static bool launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_launch_allowed(st) ? 1 : 0;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
     if (e != cudaSuccess) {
         note_cuda_error(e);

@@ -295,6 +295,14 @@ bool launch_ok() {
     note_cuda_error(e);
     return e == cudaSuccess;
 }
+bool pdl_launch_allowed(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusNone;
+}
 static bool nvtx_enabled() {
     static const bool on = [] {
         const char *v = std::getenv("TRID_NVTX");

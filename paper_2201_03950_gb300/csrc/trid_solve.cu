@@ -343,7 +343,7 @@ static bool launch_lines_tma_tw(const float *a, const float *b, const float *c, 
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_launch_allowed(st) ? 1 : 0;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, a, b, c, d, out, acc, int(L.nsys),
                                              n, int(nbatch), stages, device_status_word());
     if (e != cudaSuccess) {
@@ -426,7 +426,7 @@ static bool launch_chunk_cluster_cm(const T *a, const T *b, const T *c, const T 
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = pdl_launch_allowed(st) ? 2 : 1;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, out, acc, L, int(nstrips),
                                              tma_store, device_status_word());
     if (e != cudaSuccess) {
