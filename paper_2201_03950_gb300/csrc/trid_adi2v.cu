@@ -318,9 +318,9 @@ static bool v2_layout(const int64_t *dims, int nsteps, int every, trid_dtype dty
     l.scratch = up256(s);
     const size_t K = size_t(every);
     l.fwd = 7 * l.mesh + l.scratch;  // 6 coefficient arrays + d/w
-    // coefficients 6, transposed coefficients 4, segment u/w/delta 3K, g and gn 2,
-    // two g_w and two g_d 4, sums 6
-    l.bwd = (6 + 4 + 3 * K + 2 + 4 + 6) * l.mesh + l.scratch;
+    // coefficients 6, transposed coefficients 4, two sets of segment u/w/delta
+    // 6K, g and gn 2, two g_w and two g_d 4, sums 6; a scratch per stream
+    l.bwd = (6 + 4 + 6 * K + 2 + 4 + 6) * l.mesh + 2 * l.scratch;
     l.nseg = nsteps == 0 ? 1 : (nsteps + every - 1) / every;
     return true;
 }
@@ -434,15 +434,21 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     for (int k = 0; k < 6; ++k) co[k] = base + k * ms;
     T *tr = base + 6 * ms;           // transposed x (a, c), transposed y (a, c)
     const int K = every;
-    T *U = tr + 4 * ms;              // K states
-    T *W = U + size_t(K) * ms;       // K
-    T *D = W + size_t(K) * ms;       // K
-    T *g = D + size_t(K) * ms;
+    // two sets of the segment's u, w, delta (K each): the next segment is
+    // recomputed into one while the current one is run in reverse from the other
+    T *Us[2], *Ws[2], *Ds[2];
+    for (int b = 0; b < 2; ++b) {
+        Us[b] = tr + 4 * ms + size_t(b) * 3 * K * ms;
+        Ws[b] = Us[b] + size_t(K) * ms;
+        Ds[b] = Ws[b] + size_t(K) * ms;
+    }
+    T *g = Us[0] + size_t(6) * K * ms;
     T *gn = g + ms;
     T *gwb[2] = {gn + ms, gn + 2 * ms};  // g_w, double-buffered
     T *gdb[2] = {gn + 3 * ms, gn + 4 * ms};  // g_d, double-buffered
     T *G = gn + 5 * ms;              // 6 sums
-    char *scr = ws + (6 + 4 + 3 * size_t(K) + 2 + 4 + 6) * l.mesh;
+    char *scr = ws + (6 + 4 + 6 * size_t(K) + 2 + 4 + 6) * l.mesh;
+    char *scr2 = scr + l.scratch;
     dim3 g2, b2;
     grid2<T>(nx, ny, g2, b2);
     // the column-walking reverse kernel: V2_ROWS rows per thread
@@ -461,22 +467,58 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     if (cudaMemcpyAsync(g, guT, n * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return launch_ok(), TRID_ERR_CUDA;
     const int nseg = l.nseg;
+    // Segments are recomputed on the library's auxiliary stream and run in
+    // reverse on the caller's, ordered by events: the recomputation of segment
+    // s - 1 overlaps the reverse sweep of segment s.  Event e_set: the set-up
+    // above is done; e_rec[b]: set b holds a recomputed segment; e_rev[b]: the
+    // reverse sweep that read set b is done (set b may be overwritten).  With
+    // one segment, or without the auxiliary stream or events, everything runs
+    // on the caller's stream.
+    cudaStream_t sb = (nseg >= 2 && nsteps > 0) ? aux_stream() : nullptr;
+    cudaEvent_t ev[5] = {};
+    bool two = sb != nullptr;
+    for (int k = 0; k < 5 && two; ++k)
+        if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            two = false;
+        }
+    struct EventsGuard {
+        cudaEvent_t *e;
+        ~EventsGuard() {
+            for (int k = 0; k < 5; ++k)
+                if (e[k]) cudaEventDestroy(e[k]);
+        }
+    } guard{ev};
+    cudaEvent_t e_set = ev[0], e_rec[2] = {ev[1], ev[2]}, e_rev[2] = {ev[3], ev[4]};
+    if (two && (cudaEventRecord(e_set, st) != cudaSuccess ||
+                cudaStreamWaitEvent(sb, e_set, 0) != cudaSuccess))
+        return launch_ok(), TRID_ERR_CUDA;
     int cur = 0;  // which g_w / g_d buffers this step uses (zeroed)
-    for (int seg = nseg - 1; seg >= 0 && nsteps > 0; --seg) {
+    for (int idx = 0; idx < nseg && nsteps > 0; ++idx) {
+        const int seg = nseg - 1 - idx;
+        const int b = two ? (idx & 1) : 0;
+        T *U = Us[b], *W = Ws[b], *D = Ds[b];
         const int t0 = seg * K;
         const int t1 = (t0 + K < nsteps) ? t0 + K : nsteps;
         const int L = t1 - t0;
+        cudaStream_t rs = two ? sb : st;  // the recomputing stream
+        char *rscr = two ? scr2 : scr;
+        if (two && idx >= 2 && cudaStreamWaitEvent(sb, e_rev[b], 0) != cudaSuccess)
+            return launch_ok(), TRID_ERR_CUDA;
         if (cudaMemcpyAsync(U, ckpt + size_t(seg) * ms, n * sizeof(T), cudaMemcpyDeviceToDevice,
-                            st) != cudaSuccess)
+                            rs) != cudaSuccess)
             return launch_ok(), TRID_ERR_CUDA;
         for (int q = 0; q < L; ++q) {
             const T *up = q > 0 ? U + size_t(q - 1) * ms : nullptr;
             const T *dp = q > 0 ? D + size_t(q - 1) * ms : nullptr;
             const trid_status s = v2_recompute_step<T>(up, dp, U + size_t(q) * ms,
                                                        W + size_t(q) * ms, D + size_t(q) * ms, co,
-                                                       dims, scr, l.scratch, dt, st);
+                                                       dims, rscr, l.scratch, dt, rs);
             if (s != TRID_OK) return s;
         }
+        if (two && (cudaEventRecord(e_rec[b], sb) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, e_rec[b], 0) != cudaSuccess))
+            return launch_ok(), TRID_ERR_CUDA;
         for (int q = L - 1; q >= 0; --q) {
             T *gw = gwb[cur], *gd = gdb[cur];
             // g_w = Y^{-T} g, g_d = X^{-T} g_w: accumulated into the zeroed buffers
@@ -496,6 +538,7 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
             gn = tmp;
             cur ^= 1;
         }
+        if (two && cudaEventRecord(e_rev[b], st) != cudaSuccess) return launch_ok(), TRID_ERR_CUDA;
     }
     if (cudaMemcpyAsync(gu0, g, n * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return launch_ok(), TRID_ERR_CUDA;

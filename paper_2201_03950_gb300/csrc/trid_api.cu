@@ -25,6 +25,7 @@ size_t g_pool_size[kMaxDevices] = {};
 int *g_status_ptr[kMaxDevices] = {};
 DeviceInfo g_info[kMaxDevices];
 bool g_info_ok[kMaxDevices] = {};
+cudaStream_t g_aux_stream[kMaxDevices] = {};
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 bool g_encode_tried = false;
 }  // namespace
@@ -245,6 +246,8 @@ static void forget_device(int dev) {
     g_pool_size[dev] = 0;
     g_status_ptr[dev] = nullptr;
     g_info_ok[dev] = false;
+    if (g_aux_stream[dev]) cudaStreamDestroy(g_aux_stream[dev]);
+    g_aux_stream[dev] = nullptr;
     int k = 0;
     for (int i = 0; i < g_nocc; ++i)
         if (g_occ[i].dev != dev) g_occ[k++] = g_occ[i];
@@ -253,6 +256,21 @@ static void forget_device(int dev) {
     for (int i = 0; i < g_ncc; ++i)
         if (g_ccache[i].dev != dev) g_ccache[k++] = g_ccache[i];
     g_ncc = k;
+}
+
+cudaStream_t aux_stream() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_aux_stream[dev]) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_aux_stream[dev] = s;
+    }
+    return g_aux_stream[dev];
 }
 
 int *device_status_word() {
@@ -332,6 +350,7 @@ extern "C" trid_status trid_init(size_t pool_bytes) {
     if (!trid::device_status_word()) return TRID_ERR_CUDA;
     if (!trid::noalloc_scratch_ready()) return TRID_ERR_CUDA;
     if (!trid::encode_lines_map_ready()) return TRID_ERR_UNSUPPORTED;
+    if (!trid::aux_stream()) return TRID_ERR_CUDA;
     if (pool_bytes > 0) {
         void *p = nullptr;
         const trid_status s = trid::pool_reserve(pool_bytes, &p);

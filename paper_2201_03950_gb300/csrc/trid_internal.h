@@ -80,6 +80,12 @@ struct NvtxScope {
     ~NvtxScope();
 };
 
+// A library-owned non-blocking stream of the current device (created on first
+// use and by trid_init, destroyed by trid_finalize; nullptr if it cannot be
+// created, e.g. inside a stream capture before it exists).  Calls that use it
+// order it against the caller's stream with events only.
+cudaStream_t aux_stream();
+
 // Record a failed CUDA runtime call (read back by trid_last_cuda_error).
 void note_cuda_error(cudaError_t e);
 // cudaGetLastError() == cudaSuccess after a launch; a failure is recorded.
