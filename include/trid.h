@@ -65,7 +65,8 @@ typedef enum {
  *
  * trid_init(pool_bytes): queries and caches the current device's attributes,
  *   looks up the device status word and the allocation-free scratch array,
- *   and makes the library's scratch pool at least pool_bytes bytes (0: leave
+ *   creates the library's auxiliary stream (used by adi2v_backward), and
+ *   makes the library's scratch pool at least pool_bytes bytes (0: leave
  *   the pool as it is).  Size the pool with trid_solve_workspace_bytes for the
  *   largest problem to come; trid_solve_batch calls that fit it then never
  *   allocate, so they may be captured into a CUDA graph.  Allocates with
@@ -73,7 +74,8 @@ typedef enum {
  *   Errors: TRID_ERR_CUDA (no usable device), TRID_ERR_UNSUPPORTED (the
  *   driver lacks tensor-map encoding), TRID_ERR_ALLOC (cudaMalloc failed).
  * trid_finalize(): synchronises the current device (every stream), frees its
- *   scratch pool and forgets every cached state of that device.  Later calls
+ *   scratch pool, destroys its auxiliary stream and forgets every cached
+ *   state of that device.  Later calls
  *   work as on a fresh device (the first one re-queries the attributes and
  *   grows the pool again when it needs it).  Call it before cudaDeviceReset.
  *   Errors: TRID_ERR_CUDA (no device, or the synchronisation reported an
@@ -372,7 +374,14 @@ trid_status adi_step_batched(void *u, int64_t nbatch, const int64_t *dims, int n
  *   g_kappa = dL/dkappa, and, if g_coef is not NULL, the gradients with
  *   respect to the six coefficient arrays (ax, bx, cx, ay, by, cy; 6 packed
  *   mesh arrays) summed over the steps.  Each segment between checkpoints is
- *   recomputed forward, then run in reverse with trid_solve_batch_adjoint.
+ *   recomputed forward, then run in reverse with solves of the transposed
+ *   operators (the adjoint solves of trid_solve_batch_adjoint).  With two or
+ *   more segments the recomputation runs on the library's auxiliary stream
+ *   of the device, ordered against `stream` by events, so that segment s - 1
+ *   is recomputed while segment s runs in reverse; every piece of work is
+ *   ordered before the call's last operation on `stream`.  The auxiliary
+ *   stream is shared: calls from several host threads at once serialise on
+ *   it, and two stream captures must not include such calls at the same time.
  * Arrays are device arrays of dims[0] * dims[1] elements of `dtype`; outputs
  * must not alias inputs.  workspace (256-byte aligned) of at least
  * adi2v_workspace_bytes(dims, nsteps, every, dtype) bytes, ckpt 256-byte
