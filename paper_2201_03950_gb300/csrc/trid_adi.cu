@@ -465,13 +465,23 @@ static bool adiw_plan(const int64_t *n3, int64_t nb, double lam, AdiWPlan &p) {
     return true;
 }
 
-template <int G, int NXC = 0>
+// Planes per CTA of pass A: 32 / G (at most 16, dividing the stacked plane
+// count) when a plane is one 32-row tile, else 1.
+template <int G>
+static int xyw_ppc(const int64_t *n3, int64_t nb) {
+    if (n3[1] != WA_YT) return 1;
+    int ppc = 32 / G < 16 ? 32 / G : 16;
+    while (ppc > 1 && (n3[2] * nb) % ppc != 0) ppc /= 2;
+    return ppc;
+}
+
+template <int G, int NXC = 0, int PPC = 1>
 static bool launch_xyw(const float *u, float *e, const int64_t *n3, int64_t nb, float lam,
                        const AdiWPlan &p, cudaStream_t st, bool check_only) {
     const int C = int(n3[1] / WA_YT);
-    // X^{-1} d and Z u rows, the two received summaries, the mbarrier
-    const size_t smem = (2 * size_t(WA_YT) + 2) * size_t(n3[0]) * sizeof(float) + 16;
-    auto kern = k_adi_xyw<G, NXC>;
+    // X^{-1} d and Z u rows of the CTA's planes, the two received summaries, the mbarrier
+    const size_t smem = (2 * size_t(WA_YT) * PPC + 2) * size_t(n3[0]) * sizeof(float) + 16;
+    auto kern = k_adi_xyw<G, NXC, PPC>;
     const void *kp = reinterpret_cast<const void *>(kern);
     if (kernel_blocks_per_sm(kp, 256, smem) < 1) return false;
     if (cluster_capacity(kp, C, 256, smem) < 1) return false;
@@ -484,7 +494,7 @@ static bool launch_xyw(const float *u, float *e, const int64_t *n3, int64_t nb, 
     attr[0].val.clusterDim.z = 1;
     attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.gridDim = dim3(unsigned(C), unsigned(n3[2] * nb));
+    cfg.gridDim = dim3(unsigned(C), unsigned(n3[2] * nb / PPC));
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -501,14 +511,26 @@ static bool launch_xyw(const float *u, float *e, const int64_t *n3, int64_t nb, 
     return true;
 }
 
+// Pass A with G lanes per row: several planes per CTA when the planes are one
+// tile high, else one.
+template <int G>
+static bool launch_xyw_ppc(const float *u, float *e, const int64_t *n3, int64_t nb, float lam,
+                           const AdiWPlan &p, cudaStream_t st, bool check_only) {
+    constexpr int PMAX = 32 / G < 16 ? 32 / G : 16;
+    switch (xyw_ppc<G>(n3, nb)) {
+        case PMAX: return launch_xyw<G, 0, PMAX>(u, e, n3, nb, lam, p, st, check_only);
+        default: return launch_xyw<G, 0, 1>(u, e, n3, nb, lam, p, st, check_only);
+    }
+}
+
 static bool launch_xyw_g(const float *u, float *e, const int64_t *n3, int64_t nb, float lam,
                          const AdiWPlan &p, cudaStream_t st, bool check_only) {
     switch (p.G) {
-        case 1: return launch_xyw<1>(u, e, n3, nb, lam, p, st, check_only);
-        case 2: return launch_xyw<2>(u, e, n3, nb, lam, p, st, check_only);
-        case 4: return launch_xyw<4>(u, e, n3, nb, lam, p, st, check_only);
-        case 8: return launch_xyw<8>(u, e, n3, nb, lam, p, st, check_only);
-        case 16: return launch_xyw<16>(u, e, n3, nb, lam, p, st, check_only);
+        case 1: return launch_xyw_ppc<1>(u, e, n3, nb, lam, p, st, check_only);
+        case 2: return launch_xyw_ppc<2>(u, e, n3, nb, lam, p, st, check_only);
+        case 4: return launch_xyw_ppc<4>(u, e, n3, nb, lam, p, st, check_only);
+        case 8: return launch_xyw_ppc<8>(u, e, n3, nb, lam, p, st, check_only);
+        case 16: return launch_xyw_ppc<16>(u, e, n3, nb, lam, p, st, check_only);
         case 32:
             return n3[0] == 256 ? launch_xyw<32, 256>(u, e, n3, nb, lam, p, st, check_only)
                                 : launch_xyw<32>(u, e, n3, nb, lam, p, st, check_only);

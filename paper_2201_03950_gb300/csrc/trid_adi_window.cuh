@@ -188,7 +188,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // c handles column c: the halo summaries for the neighbours, its own rows'
 // window solve, the received summaries' responses, the store of e.
 // ---------------------------------------------------------------------------
-template <int G, int NXC>  // NXC: nx as a compile-time constant (0: run-time nx)
+// PPC planes per CTA (1, or 32 / G when a plane is one 32-row tile: then the
+// planes' rows fill the lane groups and their columns the threads of the y
+// phase); the planes of a CTA are consecutive in the stacked z order.
+template <int G, int NXC, int PPC>  // NXC: nx as a compile-time constant (0: run-time nx)
 __global__ void __launch_bounds__(256, 3)
 k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
           float c6, float bz, const __grid_constant__ XTile<float, ADI_XM> sx,
@@ -198,27 +201,32 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     constexpr unsigned FULL = 0xffffffffu;
     const int nx = NXC ? NXC : nx_arg;  // constant row strides when NXC is given
     constexpr int NGROUP = 8 * (32 / G);                      // lane groups per CTA
-    constexpr int RG = NGROUP >= WA_YT ? 1 : WA_YT / NGROUP;  // rows per group
+    constexpr int ROWS = PPC * WA_YT;                         // rows of the CTA's planes
+    constexpr int RG = NGROUP >= ROWS ? 1 : ROWS / NGROUP;    // rows per group
+    static_assert(PPC == 1 || RG * NGROUP == ROWS, "several planes fill every lane group");
     extern __shared__ __align__(16) unsigned char smem_xyw[];
-    float *sd = reinterpret_cast<float *>(smem_xyw);  // [32][nx] X^{-1} d
-    float *sz = sd + WA_YT * nx;                       // [32][nx] Z u
-    float *rh = sz + WA_YT * nx;  // [nx] h from the tile above
+    float *sd = reinterpret_cast<float *>(smem_xyw);  // [PPC * 32][nx] X^{-1} d
+    float *sz = sd + ROWS * nx;                        // [PPC * 32][nx] Z u
+    float *rh = sz + ROWS * nx;   // [nx] h from the tile above
     float *rb = rh + nx;          // [nx] b from the tile below
     uint64_t *rbar = reinterpret_cast<uint64_t *>(rb + nx);  // both have landed
     const int tid = threadIdx.x, lane = tid & 31;
     const int g = lane % G;
-    const int r0 = ((tid >> 5) * (32 / G) + lane / G) * RG;  // first row of the group
-    const bool gact = r0 < WA_YT && g * M < nx;
+    // the group's first row: row rl of plane pl of the CTA; rows r0 .. r0 + RG - 1
+    // of the CTA's shared-memory tiles
+    const int r0 = ((tid >> 5) * (32 / G) + lane / G) * RG;
+    const int pl = PPC == 1 ? 0 : r0 / WA_YT, rl = PPC == 1 ? r0 : r0 % WA_YT;
+    const bool gact = r0 < ROWS && g * M < nx;
     const int x0 = g * M;
     const int t = int(blockIdx.x), ntile = int(gridDim.x);
-    const int z = int(blockIdx.y);
+    const int z = int(blockIdx.y) * PPC + pl;  // the group's plane (stacked z)
     const int zl = z % nz;
     const bool zint = zl > 0 && zl < nz - 1;
     const int plane = nx * ny;
     const int y0 = t * WA_YT;
     const float *ut = u + size_t(z) * size_t(plane) + size_t(y0) * nx + x0;
     // elements of u and e (all planes of all meshes): the debug build's bounds
-    [[maybe_unused]] const int64_t total = int64_t(gridDim.y) * plane;
+    [[maybe_unused]] const int64_t total = int64_t(gridDim.y) * PPC * plane;
     auto ld = [&](int dy, int dz, bool ok, float (&v)[M]) {  // row y0 + dy of plane z + dz
         if (ok && TRID_BOUNDS(in_span(ut + (dz * ny + dy) * nx - u, M, total))) {
             load_contig_vec<float, M>(ut + (dz * ny + dy) * nx, v);
@@ -240,18 +248,18 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     // z - 1 lands where X^{-1} d of the row will go, plane z + 1 where its
     // Z u will go, each lane copying, and later reading, only its own chunks),
     // then the row y + 2
-    const bool yok0 = y0 + r0 - 1 >= 0;
+    const bool yok0 = y0 + rl - 1 >= 0;
     float ym[M], uc[M], yp[M], yq[M];  // rows y - 1 .. y + 2 of the group's first row
-    ld(r0 - 1, 0, gact && yok0, ym);
-    ld(r0, 0, gact, uc);
-    ld(r0 + 1, 0, gact && y0 + r0 + 1 < ny, yp);
+    ld(rl - 1, 0, gact && yok0, ym);
+    ld(rl, 0, gact, uc);
+    ld(rl + 1, 0, gact && y0 + rl + 1 < ny, yp);
 #pragma unroll
     for (int i = 0; i < RG; ++i) {
-        const int r = r0 + i;
+        const int r = rl + i;  // row of the plane; r0 + i: row of the tiles
         if (gact && zint && TRID_BOUNDS(in_span(ut + r * nx - ny * nx - u, M, total) &&
                                         in_span(ut + r * nx + ny * nx - u, M, total))) {
             const float *src = ut + r * nx;
-            float *dm = sd + r * nx, *dp = sz + r * nx;
+            float *dm = sd + (r0 + i) * nx, *dp = sz + (r0 + i) * nx;
             const int q0 = x0 >> 2;
             cp_async16(dm + (swz_chunk(q0) << 2), src - ny * nx);
             cp_async16(dm + (swz_chunk(q0 + 1) << 2), src - ny * nx + 4);
@@ -260,7 +268,7 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
         }
         cp_async_commit();
     }
-    ld(r0 + 2, 0, gact && RG > 1 && y0 + r0 + 2 < ny, yq);
+    ld(rl + 2, 0, gact && RG > 1 && y0 + rl + 2 < ny, yq);
     const int rt = sx.real_tiles;
     const bool firstx = (g == 0), lastx = (g == rt - 1);
     const int kd = g == 0 ? 0 : (g < rt - 1 ? 1 : (g == rt - 1 ? 2 : 3));
@@ -269,7 +277,8 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
 
 #pragma unroll
     for (int i = 0; i < RG; ++i) {
-        const int r = r0 + i;
+        const int r = rl + i;   // row of the plane
+        const int rs = r0 + i;  // row of the shared-memory tiles
         const int y = y0 + r;
         // the rows two and three ahead stay in flight while this row is solved
         float ny3[M];
@@ -283,8 +292,8 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
         float zs[M];
         if (gact && zint) {
             float zp[M];
-            lds8_swz(sd + r * nx, x0, zs);
-            lds8_swz(sz + r * nx, x0, zp);
+            lds8_swz(sd + rs * nx, x0, zs);
+            lds8_swz(sz + rs * nx, x0, zp);
 #pragma unroll
             for (int j = 0; j < M; ++j) zs[j] += zp[j];
         } else {
@@ -296,7 +305,7 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             float zu[M];
 #pragma unroll
             for (int j = 0; j < M; ++j) zu[j] = zint ? fmaf(-lam, zs[j], bz * uc[j]) : uc[j];
-            if (gact) sts8_swz(sz + r * nx, x0, zu);
+            if (gact) sts8_swz(sz + rs * nx, x0, zu);
         }
         const float left = __shfl_up_sync(FULL, uc[M - 1], 1, G);
         const float right = __shfl_down_sync(FULL, uc[0], 1, G);
@@ -327,7 +336,7 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             const float xs = fmaf(-xcs, xe, fmaf(-xas, xprev, ds));
             static_tile_substitute<float, M>(sx, d, xs, xe);
         }
-        if (gact) sts8_swz(sd + r * nx, x0, d);
+        if (gact) sts8_swz(sd + rs * nx, x0, d);
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             ym[j] = uc[j];
@@ -339,9 +348,13 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     __syncthreads();  // this CTA's X^{-1} d rows are complete
     const bool has_up = t > 0, has_dn = t < ntile - 1;
     if (tid == 0) mbar_expect_tx(rbar, uint32_t((has_up ? nx : 0) + (has_dn ? nx : 0)) * 4u);
-    const int c = tid;
-    const bool col = c < nx;
+    // thread (yp, c): column c of the CTA's plane yp
+    const int c = PPC == 1 ? tid : tid % nx, ypl = PPC == 1 ? 0 : tid / nx;
+    const bool col = PPC == 1 ? c < nx : ypl < PPC;
     const int cs = swz_elem(c);
+    float *sdc = sd + ypl * WA_YT * nx;  // the plane's tiles
+    const float *szc = sz + ypl * WA_YT * nx;
+    const int zy = int(blockIdx.y) * PPC + ypl;  // its plane (stacked z)
     const int kind = ntile == 1 ? 3 : (t == 0 ? 0 : (t == ntile - 1 ? 2 : 1));
     cluster_wait_acquire();  // the neighbours' mbarriers are initialised
     if (col) {
@@ -351,7 +364,7 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             float h = 0.0f;
 #pragma unroll
             for (int k = 0; k < WIN_H; ++k)
-                h = fmaf(last ? ys.Wt[2][k] : ys.Wt[1][k], sd[(WA_YT - WIN_H + k) * nx + cs], h);
+                h = fmaf(last ? ys.Wt[2][k] : ys.Wt[1][k], sdc[(WA_YT - WIN_H + k) * nx + cs], h);
             st_async_f32(cluster_map(smem_u32(rh + c), t + 1), h,
                          cluster_map(smem_u32(rbar), t + 1));
         }
@@ -360,7 +373,7 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             float b = 0.0f;
 #pragma unroll
             for (int k = 0; k < WIN_H; ++k)
-                b = fmaf(first ? ys.Wb[0][k] : ys.Wb[1][k], sd[k * nx + cs], b);
+                b = fmaf(first ? ys.Wb[0][k] : ys.Wb[1][k], sdc[k * nx + cs], b);
             st_async_f32(cluster_map(smem_u32(rb + c), t - 1), b,
                          cluster_map(smem_u32(rbar), t - 1));
         }
@@ -368,7 +381,7 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
     float v[WA_YT];
     if (col) {
 #pragma unroll
-        for (int j = 0; j < WA_YT; ++j) v[j] = sd[j * nx + cs];
+        for (int j = 0; j < WA_YT; ++j) v[j] = sdc[j * nx + cs];
         switch (kind) {  // uniform across the CTA
             case 0: tile_own_solve<0>(v, ys); break;
             case 1: tile_own_solve<1>(v, ys); break;
@@ -388,11 +401,11 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
             default: break;
         }
     }
-    if (col && TRID_BOUNDS(in_span(int64_t(z) * plane + int64_t(y0) * nx + c,
+    if (col && TRID_BOUNDS(in_span(int64_t(zy) * plane + int64_t(y0) * nx + c,
                                    int64_t(WA_YT - 1) * nx + 1, total))) {
-        float *ecol = e + size_t(z) * size_t(plane) + size_t(y0) * nx + c;
+        float *ecol = e + size_t(zy) * size_t(plane) + size_t(y0) * nx + c;
 #pragma unroll
-        for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[j] + sz[j * nx + cs];
+        for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[j] + szc[j * nx + cs];
     }
     // no CTA leaves while a summary it sent may still be in flight
     cluster_arrive_relaxed();
