@@ -43,7 +43,9 @@ CASES = [((32, 32), 6, 0.1, 40, np.float32), ((96, 96), 4, 0.1, 120, np.float32)
          # larger than one block's shared memory: 3D meshes stacked along z
          # through the two-pass kernels, or the single-mesh path
          ((64, 64, 64), 2, 0.1, 3, np.float32), ((48, 32, 64), 3, 0.2, 4, np.float64),
-         ((40, 40, 40), 2, 0.1, 2, np.float32), ((256, 200), 2, 0.1, 4, np.float32)]
+         ((40, 40, 40), 2, 0.1, 2, np.float32), ((256, 200), 2, 0.1, 4, np.float32),
+         # one 32-row tile per plane, stacked: several planes per CTA across meshes
+         ((32, 32, 32), 5, 0.1, 3, np.float32), ((64, 32, 48), 3, 0.1, 2, np.float32)]
 
 
 @pytest.mark.parametrize("dims,nb,lam,steps,dtype", CASES,

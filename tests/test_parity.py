@@ -224,7 +224,11 @@ ADI_SMALL = [((9, 7, 6), 0.1, 3), ((40, 36, 33), 0.1, 10), ((64, 64, 64), 0.1, 5
              # windowed 3D schedule (FP32: nx % 8, ny % 32, nz % 16, lambda small enough):
              # three y tile kinds, lanes beyond the x line, one z tile, many z tiles
              ((256, 96, 64), 0.1, 2), ((24, 128, 16), 0.1, 3), ((200, 160, 80), 0.1, 2),
-             ((8, 32, 32), 0.1, 2), ((64, 64, 256), 0.05, 2)]
+             ((8, 32, 32), 0.1, 2), ((64, 64, 256), 0.05, 2),
+             # one 32-row tile per plane: several planes per CTA (16, 8, 4, 2),
+             # widths that do not fill the lane groups
+             ((16, 32, 48), 0.1, 2), ((24, 32, 32), 0.1, 3), ((64, 32, 16), 0.1, 2),
+             ((120, 32, 32), 0.1, 2), ((40, 32, 80), 0.1, 2)]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
