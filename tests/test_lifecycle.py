@@ -72,3 +72,30 @@ def test_init_is_idempotent_and_only_grows(lib):
     trid.solve(ta, tb, tc, td, DIMS, 0)
     torch.cuda.synchronize()
     assert _normwise(td.cpu().numpy(), ref) <= 1e-12
+
+
+def test_finalize_then_overlapped_backward(lib):
+    """The differentiable ADI backward with several segments uses the
+    library's auxiliary stream; after trid_finalize destroys it, the next call
+    creates it again and gives the same bits as before (and as one segment,
+    which runs on the caller's stream only)."""
+    dims, lam, steps = (64, 48), 0.2, 9
+    n = dims[0] * dims[1]
+    u0 = torch.from_numpy(inputs.target_field(dims, seed=1).astype(np.float32)).cuda()
+    kap = torch.from_numpy(inputs.diffusivity_field(dims, seed=2).astype(np.float32)).cuda()
+    g = torch.from_numpy(inputs.random_rhs((n,), seed=3, dtype=np.float32)).cuda()
+
+    def grads(every):
+        _, ck = trid.adi2v_forward(u0, kap, dims, lam, steps, every)
+        gu, gk, _ = trid.adi2v_backward(g, kap, dims, lam, steps, every, ck)
+        torch.cuda.synchronize()
+        return gu.cpu().numpy(), gk.cpu().numpy()
+
+    before = grads(3)  # three segments: recomputation on the auxiliary stream
+    trid.finalize()
+    after = grads(3)
+    single = grads(9)  # one segment
+    for a, b, c in zip(before, after, single):
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, c)
+    assert trid.device_status() == 0
