@@ -407,9 +407,12 @@ k_adi_xyw(const float *u, float *e, int nx_arg, int ny, int nz, float lam,
 #pragma unroll
         for (int j = 0; j < WA_YT; ++j) ecol[j * nx] = v[j] + szc[j * nx + cs];
     }
-    // no CTA leaves while a summary it sent may still be in flight
-    cluster_arrive_relaxed();
-    cluster_wait_acquire();
+    // No cluster barrier before leaving: the only accesses to another CTA's
+    // shared memory are the st.async summaries, and their receiver does not
+    // leave before its mbarrier has counted every byte sent to it, so no CTA
+    // leaves while a write into it may still land (the sender keeps no shared
+    // memory that a neighbour reads).  Without that barrier a CTA's slot is
+    // free as soon as its own stores are issued (pass A 41.8 -> 39.3 us).
 }
 
 // Window of a z tile of kind K from the box in shared memory (sb points at
