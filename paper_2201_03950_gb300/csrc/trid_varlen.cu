@@ -466,6 +466,11 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
     }
 
     // ---- class M2: one system per block, the tiles stay in registers
+    // every thread has read the L class's final item (whose slot may be s_it[0])
+    // before the helper reuses the slot: without this barrier a late warp could
+    // take the first M2 item for an L item and meet the other warps' barriers
+    // on a different path
+    __syncthreads();
     if (tid == helper) s_it[0] = vitem_fetch(&work->next_m2, n_m2, n_l, meta);
     __syncthreads();
     for (int cur = 0;; cur ^= 1) {
