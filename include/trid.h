@@ -190,7 +190,7 @@ size_t trid_adjoint_workspace_bytes(const int64_t *dims, int ndim, int solve_dim
  *   total      host: number of elements of each array.
  *   max_len    host: an upper bound of the system lengths; it sizes the
  *              shared-memory reduced systems (TRID_ERR_UNSUPPORTED when they
- *              do not fit: about 56K rows in FP32, 28K in FP64).
+ *              do not fit: about 56K rows in FP32, 27K in FP64).
  *   u, dtype, stream  as for trid_solve_batch (u == NULL: in place in d),
  *              except that a, b, c, d and u must start on 16-byte boundaries
  *              (TRID_ERR_MISALIGNED otherwise, nothing launched).

@@ -168,10 +168,23 @@ __device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
 }
 
 // ---- shared-memory reduced systems: a level holds R rows (unit diagonal) ---
+// Rows are padded by one element per 128 bytes (row i at i + i / 32 in FP32,
+// i + i / 16 in FP64): a warp whose threads each walk M consecutive rows (a
+// stride of M elements) then hits 32 different banks, where the unpadded
+// rows put the whole warp on M-fold shared banks.
+template <typename T>
+__host__ __device__ constexpr int vpad_shift() { return sizeof(T) == 4 ? 5 : 4; }
+template <typename T>
+__host__ __device__ constexpr int64_t vpad_len(int64_t R) {  // elements for R padded rows
+    return R + (R >> vpad_shift<T>()) + 1;
+}
 template <typename T>
 struct RLevel {
-    T *a, *c, *d;
+    T *a, *c, *d;  // padded arrays: use A, C, D
     int R;
+    __device__ __forceinline__ T &A(int i) const { return a[i + (i >> vpad_shift<T>())]; }
+    __device__ __forceinline__ T &C(int i) const { return c[i + (i >> vpad_shift<T>())]; }
+    __device__ __forceinline__ T &D(int i) const { return d[i + (i >> vpad_shift<T>())]; }
 };
 
 // Tile pass of level `src` (tiles of M rows) into the reduced rows of `dst`.
@@ -184,15 +197,15 @@ __device__ void level_reduce(const RLevel<T> &src, RLevel<T> &dst) {
         for (int j = 0; j < VL_M; ++j) {
             const int i = t * VL_M + j;
             const bool in = i < src.R;
-            ra[j] = (in && i > 0) ? src.a[i] : T(0);
+            ra[j] = (in && i > 0) ? src.A(i) : T(0);
             rb[j] = T(1);
-            rc[j] = (in && i < src.R - 1) ? src.c[i] : T(0);
-            rd[j] = in ? src.d[i] : T(0);
+            rc[j] = (in && i < src.R - 1) ? src.C(i) : T(0);
+            rd[j] = in ? src.D(i) : T(0);
         }
         T as, cs, ds, ae, ce, de;
         tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-        dst.a[2 * t] = as; dst.c[2 * t] = cs; dst.d[2 * t] = ds;
-        dst.a[2 * t + 1] = ae; dst.c[2 * t + 1] = ce; dst.d[2 * t + 1] = de;
+        dst.A(2 * t) = as; dst.C(2 * t) = cs; dst.D(2 * t) = ds;
+        dst.A(2 * t + 1) = ae; dst.C(2 * t + 1) = ce; dst.D(2 * t + 1) = de;
     }
 }
 
@@ -207,17 +220,17 @@ __device__ void level_substitute(RLevel<T> &src, const RLevel<T> &dst) {
         for (int j = 0; j < VL_M; ++j) {
             const int i = t * VL_M + j;
             const bool in = i < src.R;
-            ra[j] = (in && i > 0) ? src.a[i] : T(0);
+            ra[j] = (in && i > 0) ? src.A(i) : T(0);
             rb[j] = T(1);
-            rc[j] = (in && i < src.R - 1) ? src.c[i] : T(0);
-            rd[j] = in ? src.d[i] : T(0);
+            rc[j] = (in && i < src.R - 1) ? src.C(i) : T(0);
+            rd[j] = in ? src.D(i) : T(0);
         }
         T as, cs, ds, ae, ce, de;
         tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-        tile_substitute<T, VL_M>(ra, rc, rd, dst.d[2 * t], dst.d[2 * t + 1]);
+        tile_substitute<T, VL_M>(ra, rc, rd, dst.D(2 * t), dst.D(2 * t + 1));
 #pragma unroll
         for (int j = 0; j < VL_M; ++j)
-            if (t * VL_M + j < src.R) src.d[t * VL_M + j] = rd[j];
+            if (t * VL_M + j < src.R) src.D(t * VL_M + j) = rd[j];
     }
 }
 
@@ -230,10 +243,10 @@ __device__ void level_warp_solve(RLevel<T> &lv) {
     for (int j = 0; j < VL_M; ++j) {
         const int i = lane * VL_M + j;
         const bool in = i < lv.R;
-        ra[j] = (in && i > 0) ? lv.a[i] : T(0);
+        ra[j] = (in && i > 0) ? lv.A(i) : T(0);
         rb[j] = T(1);
-        rc[j] = (in && i < lv.R - 1) ? lv.c[i] : T(0);
-        rd[j] = in ? lv.d[i] : T(0);
+        rc[j] = (in && i < lv.R - 1) ? lv.C(i) : T(0);
+        rd[j] = in ? lv.D(i) : T(0);
     }
     T as, cs, ds, ae, ce, de, xs, xe;
     tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
@@ -241,7 +254,7 @@ __device__ void level_warp_solve(RLevel<T> &lv) {
     tile_substitute<T, VL_M>(ra, rc, rd, xs, xe);
 #pragma unroll
     for (int j = 0; j < VL_M; ++j)
-        if (lane * VL_M + j < lv.R) lv.d[lane * VL_M + j] = rd[j];
+        if (lane * VL_M + j < lv.R) lv.D(lane * VL_M + j) = rd[j];
 }
 
 // Tiles of a system are aligned to 16 bytes: the system starting at element
@@ -319,7 +332,7 @@ __device__ void block_pcr(RLevel<T> &lv) {
     const int R = lv.R, nth = blockDim.x, tid = threadIdx.x;
     float cpl = 0.0f;
     for (int i = tid; i < R; i += nth)
-        cpl = fmaxf(cpl, float(fmax(fabs(lv.a[i]), fabs(lv.c[i]))));
+        cpl = fmaxf(cpl, float(fmax(fabs(lv.A(i)), fabs(lv.C(i)))));
     if (!__syncthreads_or(cpl >= negligible)) return;
     for (int s = 1; s < R; s <<= 1) {
         T na[2], nc[2], nd[2];
@@ -329,10 +342,10 @@ __device__ void block_pcr(RLevel<T> &lv) {
             const int i = tid + q * nth;
             na[q] = nc[q] = nd[q] = T(0);
             if (i < R) {
-                const T ai = lv.a[i], ci = lv.c[i], di = lv.d[i];
+                const T ai = lv.A(i), ci = lv.C(i), di = lv.D(i);
                 T am = T(0), cm = T(0), dm = T(0), ap = T(0), cp = T(0), dp = T(0);
-                if (i - s >= 0) { am = lv.a[i - s]; cm = lv.c[i - s]; dm = lv.d[i - s]; }
-                if (i + s < R) { ap = lv.a[i + s]; cp = lv.c[i + s]; dp = lv.d[i + s]; }
+                if (i - s >= 0) { am = lv.A(i - s); cm = lv.C(i - s); dm = lv.D(i - s); }
+                if (i + s < R) { ap = lv.A(i + s); cp = lv.C(i + s); dp = lv.D(i + s); }
                 const T r = rcp(T(1) - ai * cm - ci * ap);
                 na[q] = -r * (ai * am);
                 nc[q] = -r * (ci * cp);
@@ -344,7 +357,7 @@ __device__ void block_pcr(RLevel<T> &lv) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int i = tid + q * nth;
-            if (i < R) { lv.a[i] = na[q]; lv.c[i] = nc[q]; lv.d[i] = nd[q]; }
+            if (i < R) { lv.A(i) = na[q]; lv.C(i) = nc[q]; lv.D(i) = nd[q]; }
         }
         if (!__syncthreads_or(cmax >= negligible)) break;
     }
@@ -412,8 +425,9 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         const int64_t ml = max_len > VL_M2_N ? max_len : int64_t(VL_M2_N);
         int64_t R = 2 * ((ml + 2 * VL_M - 1) / VL_M);  // includes alignment padding
         for (int l = 0; l < nlevels; ++l) {
-            lv[l].a = p; lv[l].c = p + R; lv[l].d = p + 2 * R;
-            p += 3 * R;
+            const int64_t P = vpad_len<T>(R);
+            lv[l].a = p; lv[l].c = p + P; lv[l].d = p + 2 * P;
+            p += 3 * P;
             R = 2 * ((R + VL_M - 1) / VL_M);
         }
     }
@@ -445,8 +459,8 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, t, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-            lv[0].a[2 * t] = as; lv[0].c[2 * t] = cs; lv[0].d[2 * t] = ds;
-            lv[0].a[2 * t + 1] = ae; lv[0].c[2 * t + 1] = ce; lv[0].d[2 * t + 1] = de;
+            lv[0].A(2 * t) = as; lv[0].C(2 * t) = cs; lv[0].D(2 * t) = ds;
+            lv[0].A(2 * t + 1) = ae; lv[0].C(2 * t + 1) = ce; lv[0].D(2 * t + 1) = de;
         }
         longlong2 nx_meta = make_longlong2(0, 0);
         if (tid == helper && (long long)nx_item < n_l) nx_meta = meta[nx_item];
@@ -459,7 +473,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, t, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-            tile_substitute<T, VL_M>(ra, rc, rd, lv[0].d[2 * t], lv[0].d[2 * t + 1]);
+            tile_substitute<T, VL_M>(ra, rc, rd, lv[0].D(2 * t), lv[0].D(2 * t + 1));
             store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, t, rd);
         }
         __syncthreads();  // level 0 is rewritten by the next system
@@ -490,8 +504,8 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, tid, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-            lv[0].a[2 * tid] = as; lv[0].c[2 * tid] = cs; lv[0].d[2 * tid] = ds;
-            lv[0].a[2 * tid + 1] = ae; lv[0].c[2 * tid + 1] = ce; lv[0].d[2 * tid + 1] = de;
+            lv[0].A(2 * tid) = as; lv[0].C(2 * tid) = cs; lv[0].D(2 * tid) = ds;
+            lv[0].A(2 * tid + 1) = ae; lv[0].C(2 * tid + 1) = ce; lv[0].D(2 * tid + 1) = de;
         }
         longlong2 nx_meta = make_longlong2(0, 0);
         if (tid == helper && (long long)nx_item < n_m2) nx_meta = meta[n_l + nx_item];
@@ -499,7 +513,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         if (ok) block_reduced_solve<T, VL_M>(lv, nlevels);
         if (tid == helper) s_it[cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
         if (mine) {
-            tile_substitute<T, VL_M>(ra, rc, rd, lv[0].d[2 * tid], lv[0].d[2 * tid + 1]);
+            tile_substitute<T, VL_M>(ra, rc, rd, lv[0].D(2 * tid), lv[0].D(2 * tid + 1));
             store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, tid, rd);
         }
         __syncthreads();
@@ -512,10 +526,12 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         const int bar = 1 + team;  // named barrier of the team (0 is __syncthreads)
         const int thelper = tsz - 1;
         const int64_t base1 = n_l + n_m2;
-        // the team's reduced rows: R <= 2 * tsz
-        T *tbase = reinterpret_cast<T *>(smem_raw) + size_t(team) * 3 * 2 * tsz;
+        // the team's reduced rows: R <= 2 * tsz (padded; the host sizes the
+        // shared memory for every team's arrays)
+        const int64_t tp = vpad_len<T>(2 * tsz);
+        T *tbase = reinterpret_cast<T *>(smem_raw) + size_t(team) * 3 * tp;
         RLevel<T> tl;
-        tl.a = tbase; tl.c = tbase + 2 * tsz; tl.d = tbase + 4 * tsz;
+        tl.a = tbase; tl.c = tbase + tp; tl.d = tbase + 2 * tp;
         if (tt == thelper) s_team_it[team][0] = vitem_fetch(&work->next_m1, n_m1, base1, meta);
         named_barrier_sync(bar, tsz);
         for (int cur = 0;; cur ^= 1) {
@@ -535,8 +551,8 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
                 load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, tt, ra, rb, rc, rd);
                 T as, cs, ds, ae, ce, de;
                 tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-                tl.a[2 * tt] = as; tl.c[2 * tt] = cs; tl.d[2 * tt] = ds;
-                tl.a[2 * tt + 1] = ae; tl.c[2 * tt + 1] = ce; tl.d[2 * tt + 1] = de;
+                tl.A(2 * tt) = as; tl.C(2 * tt) = cs; tl.D(2 * tt) = ds;
+                tl.A(2 * tt + 1) = ae; tl.C(2 * tt + 1) = ce; tl.D(2 * tt + 1) = de;
             }
             longlong2 nx_meta = make_longlong2(0, 0);
             if (tt == thelper && (long long)nx_item < n_m1) nx_meta = meta[base1 + nx_item];
@@ -546,7 +562,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
                 s_team_it[team][cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
             named_barrier_sync(bar, tsz);
             if (mine) {
-                tile_substitute<T, VL_M>(ra, rc, rd, tl.d[2 * tt], tl.d[2 * tt + 1]);
+                tile_substitute<T, VL_M>(ra, rc, rd, tl.D(2 * tt), tl.D(2 * tt + 1));
                 store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, tt, rd);
             }
             named_barrier_sync(bar, tsz);  // the team's rows are rewritten next
@@ -598,15 +614,18 @@ static bool varlen_levels(int64_t max_len, int &nlevels, size_t &smem) {
     nlevels = 0;
     size_t rows = 0;
     for (;;) {
-        rows += 3 * size_t(R);
+        rows += 3 * size_t(vpad_len<T>(R));
         ++nlevels;
         if (R <= VL_SHORT) break;
         if (nlevels >= 8) return false;
         R = 2 * ((R + VL_M - 1) / VL_M);
     }
     smem = rows * sizeof(T);
-    const size_t teams = size_t(VL_THREADS / VL_TEAM) * 3 * 2 * VL_TEAM * sizeof(T);
-    if (smem < teams) smem = teams;
+    // the M1 teams' padded rows (either team size) share the same memory
+    for (int tsz = VL_TEAM_MIN; tsz <= VL_TEAM; tsz *= 2) {
+        const size_t teams = size_t(VL_THREADS / tsz) * 3 * size_t(vpad_len<T>(2 * tsz)) * sizeof(T);
+        if (smem < teams) smem = teams;
+    }
     return true;
 }
 
