@@ -189,7 +189,7 @@ struct RLevel {
 
 // Tile pass of level `src` (tiles of M rows) into the reduced rows of `dst`.
 template <typename T, int VL_M>
-__device__ void level_reduce(const RLevel<T> &src, RLevel<T> &dst) {
+__device__ __forceinline__ void level_reduce(const RLevel<T> &src, RLevel<T> &dst) {
     const int nt = (src.R + VL_M - 1) / VL_M;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
         T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
@@ -212,7 +212,7 @@ __device__ void level_reduce(const RLevel<T> &src, RLevel<T> &dst) {
 // Substitute the solution of `dst` (held in dst.d) back into level `src`,
 // writing src's solution into src.d.
 template <typename T, int VL_M>
-__device__ void level_substitute(RLevel<T> &src, const RLevel<T> &dst) {
+__device__ __forceinline__ void level_substitute(RLevel<T> &src, const RLevel<T> &dst) {
     const int nt = (src.R + VL_M - 1) / VL_M;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
         T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
@@ -236,7 +236,7 @@ __device__ void level_substitute(RLevel<T> &src, const RLevel<T> &dst) {
 
 // One warp solves a level of R <= 32 M rows in place (lane tiles, shuffles).
 template <typename T, int VL_M>
-__device__ void level_warp_solve(RLevel<T> &lv) {
+__device__ __forceinline__ void level_warp_solve(RLevel<T> &lv) {
     const int lane = threadIdx.x & 31;
     T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
 #pragma unroll
@@ -327,7 +327,7 @@ __device__ __forceinline__ void store_sys_tile(T *out, int accumulate, int64_t s
 // them are below 2^-(p+4) (p the significand bits) the remaining rounds change
 // no value by more than 1/16 ulp, and the level's d holds the solution.
 template <typename T>
-__device__ void block_pcr(RLevel<T> &lv) {
+__device__ __forceinline__ void block_pcr(RLevel<T> &lv) {
     constexpr float negligible = sizeof(T) == 4 ? 3.7252903e-09f : 6.9388939e-18f;
     const int R = lv.R, nth = blockDim.x, tid = threadIdx.x;
     float cpl = 0.0f;
@@ -363,23 +363,61 @@ __device__ void block_pcr(RLevel<T> &lv) {
     }
 }
 
-// Solve the reduced system held in level 0 (rows R already written, block
+// Level l of the shared-memory hierarchy (R rows of data): its arrays sit
+// after the padded arrays of the levels above it, each sized for the longest
+// admissible system (level 0 holds rmax0 rows).  The pointers are formed from
+// the shared-memory base at every use (never kept in an indexed array, which
+// would put them in local memory), so the accesses compile to shared-memory
+// loads and stores rather than generic ones.
+template <typename T, int VL_M>
+__device__ __forceinline__ RLevel<T> level_at(T *sbase, int rmax0, int l, int R) {
+    int64_t off = 0, rm = rmax0;
+    for (int k = 0; k < l; ++k) {
+        off += 3 * vpad_len<T>(rm);
+        rm = 2 * ((rm + VL_M - 1) / VL_M);
+    }
+    const int64_t P = vpad_len<T>(rm);
+    RLevel<T> v;
+    v.a = sbase + off;
+    v.c = v.a + P;
+    v.d = v.a + 2 * P;
+    v.R = R;
+    return v;
+}
+
+// Rows of level l of a system whose level 0 holds R0 rows.
+template <int VL_M>
+__device__ __forceinline__ int level_rows(int R0, int l) {
+    int R = R0;
+    for (int k = 0; k < l; ++k) R = 2 * ((R + VL_M - 1) / VL_M);
+    return R;
+}
+
+// Solve the reduced system held in level 0 (R0 rows already written, block
 // synchronised): tile passes in shared memory while it is longer than two rows
 // per thread, the block PCR on the top level, then substitution back down to
-// level 0 (whose solution is then in lv[0].d).  All threads of the block call it.
+// level 0 (whose solution is then in its d).  All threads of the block call it.
 template <typename T, int VL_M>
-__device__ void block_reduced_solve(RLevel<T> *lv, int nlevels) {
-    int top = 0;
-    while (lv[top].R > 2 * int(blockDim.x) && top + 1 < nlevels) {
-        lv[top + 1].R = 2 * ((lv[top].R + VL_M - 1) / VL_M);
-        level_reduce<T, VL_M>(lv[top], lv[top + 1]);
+__device__ __forceinline__ void block_reduced_solve(T *sbase, int rmax0, int R0, int nlevels) {
+    int top = 0, R = R0;
+    while (R > 2 * int(blockDim.x) && top + 1 < nlevels) {
+        const int Rn = 2 * ((R + VL_M - 1) / VL_M);
+        RLevel<T> dst = level_at<T, VL_M>(sbase, rmax0, top + 1, Rn);
+        level_reduce<T, VL_M>(level_at<T, VL_M>(sbase, rmax0, top, R), dst);
         __syncthreads();
         ++top;
+        R = Rn;
     }
-    block_pcr<T>(lv[top]);
+    {
+        RLevel<T> t = level_at<T, VL_M>(sbase, rmax0, top, R);
+        block_pcr<T>(t);
+    }
     __syncthreads();
     for (int l = top - 1; l >= 0; --l) {
-        level_substitute<T, VL_M>(lv[l], lv[l + 1]);
+        const int Rl = level_rows<VL_M>(R0, l);
+        RLevel<T> src = level_at<T, VL_M>(sbase, rmax0, l, Rl);
+        level_substitute<T, VL_M>(src, level_at<T, VL_M>(sbase, rmax0, l + 1,
+                                                         2 * ((Rl + VL_M - 1) / VL_M)));
         __syncthreads();
     }
 }
@@ -419,18 +457,9 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
     __shared__ VItem s_it[2];
     __shared__ VItem s_team_it[VL_THREADS / VL_TEAM_MIN][2];
     // level sizes for the longest admissible system (at least an M2 system)
-    RLevel<T> lv[8];
-    {
-        T *p = reinterpret_cast<T *>(smem_raw);
-        const int64_t ml = max_len > VL_M2_N ? max_len : int64_t(VL_M2_N);
-        int64_t R = 2 * ((ml + 2 * VL_M - 1) / VL_M);  // includes alignment padding
-        for (int l = 0; l < nlevels; ++l) {
-            const int64_t P = vpad_len<T>(R);
-            lv[l].a = p; lv[l].c = p + P; lv[l].d = p + 2 * P;
-            p += 3 * P;
-            R = 2 * ((R + VL_M - 1) / VL_M);
-        }
-    }
+    T *const sbase = reinterpret_cast<T *>(smem_raw);
+    const int rmax0 = int(2 * (((max_len > VL_M2_N ? max_len : int64_t(VL_M2_N)) + 2 * VL_M - 1) /
+                               VL_M));  // includes alignment padding
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int helper = blockDim.x - 1;
@@ -453,19 +482,19 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         const int pad = sys_pad<T>(s0);
         const int64_t ntiles = ok ? (n + pad + VL_M - 1) / VL_M : 0;
         // pass 1: tile reduction of the system into level 0
-        lv[0].R = int(2 * ntiles);
+        const RLevel<T> l0 = level_at<T, VL_M>(sbase, rmax0, 0, int(2 * ntiles));
         for (int64_t t = tid; t < ntiles; t += blockDim.x) {
             T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
             load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, t, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-            lv[0].A(2 * t) = as; lv[0].C(2 * t) = cs; lv[0].D(2 * t) = ds;
-            lv[0].A(2 * t + 1) = ae; lv[0].C(2 * t + 1) = ce; lv[0].D(2 * t + 1) = de;
+            l0.A(2 * t) = as; l0.C(2 * t) = cs; l0.D(2 * t) = ds;
+            l0.A(2 * t + 1) = ae; l0.C(2 * t + 1) = ce; l0.D(2 * t + 1) = de;
         }
         longlong2 nx_meta = make_longlong2(0, 0);
         if (tid == helper && (long long)nx_item < n_l) nx_meta = meta[nx_item];
         __syncthreads();
-        if (ok) block_reduced_solve<T, VL_M>(lv, nlevels);
+        if (ok) block_reduced_solve<T, VL_M>(sbase, rmax0, l0.R, nlevels);
         if (tid == helper) s_it[cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
         // pass 2: recompute every tile and substitute its end values
         for (int64_t t = tid; t < ntiles; t += blockDim.x) {
@@ -473,7 +502,7 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
             load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, t, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-            tile_substitute<T, VL_M>(ra, rc, rd, lv[0].D(2 * t), lv[0].D(2 * t + 1));
+            tile_substitute<T, VL_M>(ra, rc, rd, l0.D(2 * t), l0.D(2 * t + 1));
             store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, t, rd);
         }
         __syncthreads();  // level 0 is rewritten by the next system
@@ -499,21 +528,21 @@ k_varlen_solve(const T *__restrict__ a, const T *__restrict__ b, const T *__rest
         const int ntiles = ok ? int((n + pad + VL_M - 1) / VL_M) : 0;  // <= blockDim.x
         const bool mine = tid < ntiles;
         T ra[VL_M], rb[VL_M], rc[VL_M], rd[VL_M];
-        lv[0].R = 2 * ntiles;
+        const RLevel<T> l0 = level_at<T, VL_M>(sbase, rmax0, 0, 2 * ntiles);
         if (mine) {
             load_sys_tile<T, VL_M>(a, b, c, d, s0, n, pad, total, tid, ra, rb, rc, rd);
             T as, cs, ds, ae, ce, de;
             tile_reduce<T, VL_M>(ra, rb, rc, rd, as, cs, ds, ae, ce, de);
-            lv[0].A(2 * tid) = as; lv[0].C(2 * tid) = cs; lv[0].D(2 * tid) = ds;
-            lv[0].A(2 * tid + 1) = ae; lv[0].C(2 * tid + 1) = ce; lv[0].D(2 * tid + 1) = de;
+            l0.A(2 * tid) = as; l0.C(2 * tid) = cs; l0.D(2 * tid) = ds;
+            l0.A(2 * tid + 1) = ae; l0.C(2 * tid + 1) = ce; l0.D(2 * tid + 1) = de;
         }
         longlong2 nx_meta = make_longlong2(0, 0);
         if (tid == helper && (long long)nx_item < n_m2) nx_meta = meta[n_l + nx_item];
         __syncthreads();
-        if (ok) block_reduced_solve<T, VL_M>(lv, nlevels);
+        if (ok) block_reduced_solve<T, VL_M>(sbase, rmax0, l0.R, nlevels);
         if (tid == helper) s_it[cur ^ 1] = VItem{(long long)nx_item, nx_meta.x, nx_meta.y};
         if (mine) {
-            tile_substitute<T, VL_M>(ra, rc, rd, lv[0].D(2 * tid), lv[0].D(2 * tid + 1));
+            tile_substitute<T, VL_M>(ra, rc, rd, l0.D(2 * tid), l0.D(2 * tid + 1));
             store_sys_tile<T, VL_M>(out, accumulate, s0, n, pad, total, tid, rd);
         }
         __syncthreads();
