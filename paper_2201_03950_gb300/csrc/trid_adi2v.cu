@@ -106,11 +106,10 @@ __global__ void k_v2_transpose(const T *__restrict__ ax, const T *__restrict__ c
 
 // The explicit part of a recomputed step, from the previous step's state and
 // increment: u = up + dp (when dp is given; else u is read as is), written to
-// u; d = lam (Lx + Ly) u as k_v2_rhs; dz zeroed (the step's delta, which the
-// y solve then accumulates into).
+// u; d = lam (Lx + Ly) u as k_v2_rhs.
 template <typename T>
 __global__ void k_v2_rhs_keep(const T *up, const T *dp, T *u, const T *ax, const T *cx,
-                              const T *ay, const T *cy, T *d, T *dz, int nx, int ny) {
+                              const T *ay, const T *cy, T *d, int nx, int ny) {
     pdl_wait();
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,7 +123,6 @@ __global__ void k_v2_rhs_keep(const T *up, const T *dp, T *u, const T *ax, const
             v += -cy[p] * (U(p + nx) - uc) + ay[p] * (uc - U(p - nx));
         }
         d[p] = v;
-        dz[p] = T(0);
         if (dp) u[p] = uc;
     }
 }
@@ -132,9 +130,8 @@ __global__ void k_v2_rhs_keep(const T *up, const T *dp, T *u, const T *ax, const
 // Reverse of the explicit part and of the identity path, plus the summed
 // coefficient gradients:  gn = g + S^T gm  (gm = g_d on the interior).
 // Gather form: point q collects the stencil rows p = q, q +- 1, q +- nx that
-// read u_q.  w and dl are the step's X^{-1} d and delta; gd_next and gw_next
-// (the other buffers of the pair) are zeroed for the next step's accumulating
-// adjoint solves.  Per point p the step's coefficient gradients are
+// read u_q.  w and dl are the step's X^{-1} d and delta.  Per point p the
+// step's coefficient gradients are
 //   a_x: -g_d,p w_{p-1} + gm_p (u_p - u_{p-1}),  b_x: -g_d,p w_p,
 //   c_x: -g_d,p w_{p+1} + gm_p (u_p - u_{p+1})   (y alike with g_w, delta).
 // COEF: G_k += each of the six (the caller wants them); otherwise only the
@@ -150,8 +147,8 @@ constexpr int V2_ROWS = 8;
 template <typename T, bool COEF>
 __global__ void __launch_bounds__(256)
 k_v2_rhs_adj(const T *g, const T *gd, const T *gw, const T *u, const T *w, const T *dl,
-             const T *ax, const T *cx, const T *ay, const T *cy, T *G, T *gn, T *gd_next,
-             T *gw_next, int nx, int ny, size_t n) {
+             const T *ax, const T *cx, const T *ay, const T *cy, T *G, T *gn, int nx, int ny,
+             size_t n) {
     pdl_wait();
     // n: element stride between the arrays of G
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,8 +225,6 @@ k_v2_rhs_adj(const T *g, const T *gd, const T *gw, const T *u, const T *w, const
                 G[n + p] += f;
             }
         }
-        gd_next[p] = T(0);
-        gw_next[p] = T(0);
         // slide the column window down one row
         u_m = u_c; u_c = u_p; u_p = col(u, j + 2);
         d_m = d_c; d_c = d_p; d_p = col(dl, j + 2);
@@ -319,8 +314,8 @@ static bool v2_layout(const int64_t *dims, int nsteps, int every, trid_dtype dty
     const size_t K = size_t(every);
     l.fwd = 7 * l.mesh + l.scratch;  // 6 coefficient arrays + d/w
     // coefficients 6, transposed coefficients 4, two sets of segment u/w/delta
-    // 6K, g and gn 2, two g_w and two g_d 4, sums 6; a scratch per stream
-    l.bwd = (6 + 4 + 6 * K + 2 + 4 + 6) * l.mesh + 2 * l.scratch;
+    // 6K, g and gn 2, g_w and g_d 2, sums 6; a scratch per stream
+    l.bwd = (6 + 4 + 6 * K + 2 + 2 + 6) * l.mesh + 2 * l.scratch;
     l.nseg = nsteps == 0 ? 1 : (nsteps + every - 1) / every;
     return true;
 }
@@ -372,9 +367,9 @@ static trid_status v2_forward_step(T *u, T *dw, const T *const co[6], const int6
 // A step recomputed by the backward, keeping u (at u; formed from the
 // previous state up and increment dp unless dp is NULL), w = X^{-1} d (at w)
 // and delta = Y^{-1} w (at dl).  Three launches: the explicit part (which also
-// writes u and zeroes dl), the x solve in place, the y solve accumulated into
-// dl (w stays intact).  u + delta is formed by the next step's first kernel,
-// with the same rounding as the forward's accumulating y solve.
+// writes u), the x solve in place, the y solve stored into dl (w stays
+// intact).  u + delta is formed by the next step's first kernel, with the
+// same rounding as the forward's accumulating y solve.
 template <typename T>
 static trid_status v2_recompute_step(const T *up, const T *dp, T *u, T *w, T *dl,
                                      const T *const co[6], const int64_t *dims, char *scr,
@@ -382,13 +377,12 @@ static trid_status v2_recompute_step(const T *up, const T *dp, T *u, T *w, T *dl
     const int nx = int(dims[0]), ny = int(dims[1]);
     dim3 g, b;
     grid2<T>(nx, ny, g, b);
-    if (!launch_pdl(k_v2_rhs_keep<T>, g, b, st, up, dp, u, co[0], co[2], co[3], co[5], w, dl, nx,
-                    ny))
+    if (!launch_pdl(k_v2_rhs_keep<T>, g, b, st, up, dp, u, co[0], co[2], co[3], co[5], w, nx, ny))
         return TRID_ERR_CUDA;
     trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], w, nullptr, dims, 2, 0, dt, scr,
                                         scr_bytes, st);
     if (s != TRID_OK) return s;
-    return trid_solve_batch_ws(co[3], co[4], co[5], w, dl, dims, 2, 1, dt, scr, scr_bytes, st);
+    return solve_into_ws(co[3], co[4], co[5], w, dl, dims, 2, 1, dt, scr, scr_bytes, st);
 }
 
 template <typename T>
@@ -444,10 +438,10 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     }
     T *g = Us[0] + size_t(6) * K * ms;
     T *gn = g + ms;
-    T *gwb[2] = {gn + ms, gn + 2 * ms};  // g_w, double-buffered
-    T *gdb[2] = {gn + 3 * ms, gn + 4 * ms};  // g_d, double-buffered
-    T *G = gn + 5 * ms;              // 6 sums
-    char *scr = ws + (6 + 4 + 6 * size_t(K) + 2 + 4 + 6) * l.mesh;
+    T *const gw = gn + ms;  // g_w and g_d of the current step (stored by its adjoint solves)
+    T *const gd = gn + 2 * ms;
+    T *G = gn + 3 * ms;     // 6 sums
+    char *scr = ws + (6 + 4 + 6 * size_t(K) + 2 + 2 + 6) * l.mesh;
     char *scr2 = scr + l.scratch;
     dim3 g2, b2;
     grid2<T>(nx, ny, g2, b2);
@@ -460,9 +454,6 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     if (!launch_ok()) return TRID_ERR_CUDA;
     // the six coefficient-gradient sums, or (no g_coef wanted) the two face sums
     if (cudaMemsetAsync(G, 0, (gcoef ? 6 : 2) * ms * sizeof(T), st) != cudaSuccess)
-        return launch_ok(), TRID_ERR_CUDA;
-    if (cudaMemsetAsync(gwb[0], 0, ms * sizeof(T), st) != cudaSuccess ||
-        cudaMemsetAsync(gdb[0], 0, ms * sizeof(T), st) != cudaSuccess)
         return launch_ok(), TRID_ERR_CUDA;
     if (cudaMemcpyAsync(g, guT, n * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return launch_ok(), TRID_ERR_CUDA;
@@ -493,7 +484,6 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
     if (two && (cudaEventRecord(e_set, st) != cudaSuccess ||
                 cudaStreamWaitEvent(sb, e_set, 0) != cudaSuccess))
         return launch_ok(), TRID_ERR_CUDA;
-    int cur = 0;  // which g_w / g_d buffers this step uses (zeroed)
     for (int idx = 0; idx < nseg && nsteps > 0; ++idx) {
         const int seg = nseg - 1 - idx;
         const int b = two ? (idx & 1) : 0;
@@ -520,23 +510,20 @@ static trid_status v2_backward(const T *guT, T *gu0, T *gk, T *gcoef, const T *k
                     cudaStreamWaitEvent(st, e_rec[b], 0) != cudaSuccess))
             return launch_ok(), TRID_ERR_CUDA;
         for (int q = L - 1; q >= 0; --q) {
-            T *gw = gwb[cur], *gd = gdb[cur];
-            // g_w = Y^{-T} g, g_d = X^{-T} g_w: accumulated into the zeroed buffers
-            trid_status s = trid_solve_batch_ws(tr + 2 * ms, co[4], tr + 3 * ms, g, gw, dims, 2,
-                                                1, dt, scr, l.scratch, st);
+            // g_w = Y^{-T} g, g_d = X^{-T} g_w, each stored into its own buffer
+            // (g and g_w stay intact for the reverse stencil kernel)
+            trid_status s = solve_into_ws(tr + 2 * ms, co[4], tr + 3 * ms, g, gw, dims, 2, 1, dt,
+                                          scr, l.scratch, st);
             if (s != TRID_OK) return s;
-            s = trid_solve_batch_ws(tr, co[1], tr + ms, gw, gd, dims, 2, 0, dt, scr, l.scratch,
-                                    st);
+            s = solve_into_ws(tr, co[1], tr + ms, gw, gd, dims, 2, 0, dt, scr, l.scratch, st);
             if (s != TRID_OK) return s;
             auto kern = gcoef ? k_v2_rhs_adj<T, true> : k_v2_rhs_adj<T, false>;
             if (!launch_pdl(kern, ga, b2, st, g, gd, gw, U + size_t(q) * ms, W + size_t(q) * ms,
-                            D + size_t(q) * ms, co[0], co[2], co[3], co[5], G, gn, gdb[cur ^ 1],
-                            gwb[cur ^ 1], nx, ny, ms))
+                            D + size_t(q) * ms, co[0], co[2], co[3], co[5], G, gn, nx, ny, ms))
                 return TRID_ERR_CUDA;
             T *tmp = g;
             g = gn;
             gn = tmp;
-            cur ^= 1;
         }
         if (two && cudaEventRecord(e_rev[b], st) != cudaSuccess) return launch_ok(), TRID_ERR_CUDA;
     }

@@ -17,6 +17,14 @@ inline bool is_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p)
 // too small.  Shared by all calls on that device.
 trid_status pool_reserve(size_t bytes, void **out);
 
+// As trid_solve_batch_ws, but the solution is stored into `out` (which must
+// not overlap a, b, c or d) rather than into d or added into u; d is only
+// read.  Used by the differentiable ADI, whose adjoint solves would otherwise
+// accumulate into buffers zeroed every step.
+trid_status solve_into_ws(const void *a, const void *b, const void *c, const void *d, void *out,
+                          const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
+                          void *workspace, size_t workspace_bytes, cudaStream_t st);
+
 // Cached attributes of the current device (queried on first use per device).
 struct DeviceInfo {
     int sm_count;

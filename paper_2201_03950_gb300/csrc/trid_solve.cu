@@ -590,20 +590,23 @@ static trid_status check_solve_args(const void *a, const void *b, const void *c,
     return TRID_OK;
 }
 
+// x into `out`: stored (acc = 0) or added (acc = 1); every path reads d only.
+static trid_status solve_dispatch_out(const void *a, const void *b, const void *c, const void *d,
+                                      void *out, int acc, const Lines &L, trid_dtype dtype,
+                                      char *ws, size_t ws_bytes, cudaStream_t st) {
+    if (dtype == TRID_F32)
+        return solve_lines<float>(static_cast<const float *>(a), static_cast<const float *>(b),
+                                  static_cast<const float *>(c), static_cast<const float *>(d),
+                                  static_cast<float *>(out), acc, L, ws, ws_bytes, st);
+    return solve_lines<double>(static_cast<const double *>(a), static_cast<const double *>(b),
+                               static_cast<const double *>(c), static_cast<const double *>(d),
+                               static_cast<double *>(out), acc, L, ws, ws_bytes, st);
+}
+
 static trid_status solve_dispatch(const void *a, const void *b, const void *c, void *d, void *u,
                                   const Lines &L, trid_dtype dtype, char *ws, size_t ws_bytes,
                                   cudaStream_t st) {
-    const int acc = u ? 1 : 0;
-    if (dtype == TRID_F32) {
-        float *out = static_cast<float *>(u ? u : d);
-        return solve_lines<float>(static_cast<const float *>(a), static_cast<const float *>(b),
-                                  static_cast<const float *>(c), static_cast<const float *>(d),
-                                  out, acc, L, ws, ws_bytes, st);
-    }
-    double *out = static_cast<double *>(u ? u : d);
-    return solve_lines<double>(static_cast<const double *>(a), static_cast<const double *>(b),
-                               static_cast<const double *>(c), static_cast<const double *>(d),
-                               out, acc, L, ws, ws_bytes, st);
+    return solve_dispatch_out(a, b, c, d, u ? u : d, u ? 1 : 0, L, dtype, ws, ws_bytes, st);
 }
 
 // Argument check, scratch size and dispatch for a caller that supplies its own
@@ -635,6 +638,22 @@ trid_status solve_with_scratch(const void *a, const void *b, const void *c, void
     if (need > scratch_bytes)  // OK if a one-pass kernel took it, else ALLOC with nothing launched
         return solve_dispatch(a, b, c, d, u, L, dtype, nullptr, 0, st);
     return solve_dispatch(a, b, c, d, u, L, dtype, static_cast<char *>(scratch), scratch_bytes, st);
+}
+
+trid_status solve_into_ws(const void *a, const void *b, const void *c, const void *d, void *out,
+                          const int64_t *dims, int ndim, int solve_dim, trid_dtype dtype,
+                          void *workspace, size_t workspace_bytes, cudaStream_t st) {
+    Lines L;
+    size_t esz;
+    if (!out) return TRID_ERR_INVALID_ARG;
+    trid_status s = check_solve_args(a, b, c, const_cast<void *>(d), out, dims, ndim, solve_dim,
+                                     dtype, L, esz);
+    if (s != TRID_OK || L.nsys == 0 || L.n == 0) return s;
+    const size_t need = solve_ws_bytes(L, dtype);
+    if (need > 0 && (workspace == nullptr || workspace_bytes < need)) return TRID_ERR_ALLOC;
+    if (need > 0 && (reinterpret_cast<uintptr_t>(workspace) % 256) != 0) return TRID_ERR_MISALIGNED;
+    return solve_dispatch_out(a, b, c, d, out, 0, L, dtype, static_cast<char *>(workspace),
+                              workspace_bytes, st);
 }
 
 }  // namespace trid
