@@ -21,7 +21,7 @@
 // The coefficient arrays do not change over the steps: the transposed
 // operators (sub-diagonal c_{i-1}, super-diagonal a_{i+1}) are formed once
 // per backward call, each step's two adjoint solves are plain solves of them
-// accumulated into zeroed buffers (so g and g_w stay intact), and one kernel
+// stored into their own buffers (so g and g_w stay intact), and one kernel
 // per step forms the stencil's reverse, every coefficient gradient of the step
 // and their sums over the steps (taken to kappa once at the end).
 //
@@ -33,6 +33,7 @@
 #include <cstdint>
 
 #include "../../include/trid.h"
+#include "trid_device.cuh"
 #include "trid_internal.h"
 #include "trid_tma.cuh"
 
@@ -86,6 +87,152 @@ __global__ void k_v2_rhs(const T *u, const T *ax, const T *cx, const T *ay, cons
         d[p] = v;
     }
 }
+
+// The explicit part fused with the x solve, one block per x line (row j):
+// w = X^{-1} d with d as k_v2_rhs.  KEEP (a recomputed step): u = up + dp is
+// formed on the fly for rows j - 1 .. j + 1 and row j is written to u, as
+// k_v2_rhs_keep; without KEEP, u is read.  Thread t owns columns [8 t, 8 t +
+// 8) (nx % 8 == 0, nx <= 1024, so at most 128 threads): the RHS and the tile
+// pass of Section 3.1 in registers, the 2 nx / 8 reduced rows in shared memory
+// (padded by one element per 128 bytes: warp 0's lanes walk them in runs of
+// 8) solved by warp 0 (tiles of 8 reduced rows, then the shuffled reduced
+// solve of 32 lanes), then every tile substituted and stored.  d never goes
+// to memory, and the step saves a launch.
+constexpr int V2X_M = 8;
+constexpr int V2X_MAXT = 128;  // threads (tiles) per line: nx <= 1024
+
+template <typename T>
+__device__ __forceinline__ int v2x_pad(int i) {
+    return i + (i >> (sizeof(T) == 4 ? 5 : 4));
+}
+
+template <typename T, bool KEEP>
+__global__ void __launch_bounds__(V2X_MAXT)
+k_v2_rhs_x(const T *up, const T *dp, T *u, const T *ax, const T *bx, const T *cx, const T *ay,
+           const T *cy, T *w, int nx, int ny, int vec_u) {
+    constexpr int M = V2X_M;
+    constexpr int RP = 2 * V2X_MAXT + (2 * V2X_MAXT) / (sizeof(T) == 4 ? 32 : 16) + 1;
+    __shared__ T ra_s[RP], rc_s[RP], rd_s[RP];  // reduced rows (padded)
+    __shared__ T edge_l[V2X_MAXT], edge_r[V2X_MAXT];  // u at each tile's first / last column
+    pdl_wait();
+    const int t = threadIdx.x, lane = t & 31;
+    const int nt = nx / M;           // tiles of the line
+    const int nthr = int(blockDim.x);  // >= nt, a multiple of 32
+    const bool own = t < nt;
+    const int x0 = t * M;
+    for (int j = blockIdx.x; j < ny; j += gridDim.x) {
+        const size_t rowp = size_t(j) * nx;
+        auto ld = [&](const T *q, T (&r)[M]) {  // vector loads unless u is unaligned
+            if (vec_u) {
+                load_contig_vec<T, M>(q, r);
+            } else {
+#pragma unroll
+                for (int k = 0; k < M; ++k) r[k] = q[k];
+            }
+        };
+        auto ldrow = [&](int jj, T (&r)[M]) {  // u of row jj at the thread's columns
+            if (KEEP && dp) {
+                T e[M];
+                ld(up + size_t(jj) * nx + x0, r);
+                ld(dp + size_t(jj) * nx + x0, e);
+#pragma unroll
+                for (int k = 0; k < M; ++k) r[k] = r[k] + e[k];
+            } else {
+                ld(u + size_t(jj) * nx + x0, r);
+            }
+        };
+        T uc[M], d[M], a[M], b[M], c[M];
+        if (own) {
+            ldrow(j, uc);
+            edge_l[t] = uc[0];
+            edge_r[t] = uc[M - 1];
+        }
+        __syncthreads();
+        if (own) {
+            const bool jin = j > 0 && j < ny - 1;
+            T um[M], upn[M], axv[M], cxv[M], ayv[M], cyv[M];
+            if (jin) {
+                ldrow(j - 1, um);
+                ldrow(j + 1, upn);
+                load_contig_vec<T, M>(ay + rowp + x0, ayv);
+                load_contig_vec<T, M>(cy + rowp + x0, cyv);
+            }
+            load_contig_vec<T, M>(ax + rowp + x0, axv);
+            load_contig_vec<T, M>(cx + rowp + x0, cxv);
+            load_contig_vec<T, M>(bx + rowp + x0, b);
+            const T left = t > 0 ? edge_r[t - 1] : T(0);
+            const T right = t + 1 < nt ? edge_l[t + 1] : T(0);
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int i = x0 + k;
+                T v = T(0);
+                if (jin && i > 0 && i < nx - 1) {
+                    const T ul = k == 0 ? left : uc[k - 1];
+                    const T ur = k == M - 1 ? right : uc[k + 1];
+                    v = -cxv[k] * (ur - uc[k]) + axv[k] * (uc[k] - ul);
+                    v += -cyv[k] * (upn[k] - uc[k]) + ayv[k] * (uc[k] - um[k]);
+                }
+                d[k] = v;
+                a[k] = i == 0 ? T(0) : axv[k];
+                c[k] = i == nx - 1 ? T(0) : cxv[k];
+            }
+            if (KEEP && dp) {
+                if (vec_u) {
+                    store_contig_vec<T, M>(u + rowp + x0, uc);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < M; ++k) u[rowp + x0 + k] = uc[k];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < M; ++k) { a[k] = T(0); b[k] = T(1); c[k] = T(0); d[k] = T(0); }
+        }
+        T as, cs, ds, ae, ce, de;
+        tile_reduce<T, M>(a, b, c, d, as, cs, ds, ae, ce, de);
+        ra_s[v2x_pad<T>(2 * t)] = as; rc_s[v2x_pad<T>(2 * t)] = cs; rd_s[v2x_pad<T>(2 * t)] = ds;
+        ra_s[v2x_pad<T>(2 * t + 1)] = ae; rc_s[v2x_pad<T>(2 * t + 1)] = ce;
+        rd_s[v2x_pad<T>(2 * t + 1)] = de;
+        __syncthreads();
+        if (t < 32) {
+            // the 2 nthr reduced rows: lane l takes rows [8 l, 8 l + 8)
+            const int R = 2 * nthr;
+            T qa[M], qb[M], qc[M], qd[M];
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int i = lane * M + k;
+                const bool in = i < R;
+                qa[k] = (in && i > 0) ? ra_s[v2x_pad<T>(i)] : T(0);
+                qb[k] = T(1);
+                qc[k] = (in && i < R - 1) ? rc_s[v2x_pad<T>(i)] : T(0);
+                qd[k] = in ? rd_s[v2x_pad<T>(i)] : T(0);
+            }
+            T qas, qcs, qds, qae, qce, qde, xs, xe;
+            tile_reduce<T, M>(qa, qb, qc, qd, qas, qcs, qds, qae, qce, qde);
+            group_solve<T, 32>(qas, qcs, qds, qae, qce, qde, lane, xs, xe);
+            tile_substitute<T, M>(qa, qc, qd, xs, xe);
+#pragma unroll
+            for (int k = 0; k < M; ++k)
+                if (lane * M + k < R) rd_s[v2x_pad<T>(lane * M + k)] = qd[k];
+        }
+        __syncthreads();
+        if (own) {
+            tile_substitute<T, M>(a, c, d, rd_s[v2x_pad<T>(2 * t)], rd_s[v2x_pad<T>(2 * t + 1)]);
+            store_contig_vec<T, M>(w + rowp + x0, d);
+        }
+        __syncthreads();  // the shared rows are rewritten for the next line
+    }
+}
+
+// The fused explicit part + x solve takes lines of nx a multiple of 8 up to
+// 1024.  The choice depends on nx alone, so that the forward and the
+// backward's recomputation (separate calls) always run the same arithmetic;
+// the workspace arrays are 256-byte aligned, and u (the caller's) is read
+// with scalar loads when it is not on a 16-byte boundary.
+static bool v2x_fits(int nx) {
+    return nx % V2X_M == 0 && nx / V2X_M <= V2X_MAXT && nx >= 2 * V2X_M;
+}
+
 
 // The transposed operators: A^T has sub-diagonal c_{i-1} and super-diagonal
 // a_{i+1} (the diagonal is b).
@@ -343,6 +490,16 @@ static bool launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
     return true;
 }
 
+template <typename T, bool KEEP>
+static bool launch_v2x(const T *up, const T *dp, T *u, const T *const co[6], T *w, int nx, int ny,
+                       cudaStream_t st) {
+    const int threads = (nx / V2X_M + 31) / 32 * 32;
+    const int vec_u = is_aligned16(u) && (!up || is_aligned16(up)) && (!dp || is_aligned16(dp));
+    const dim3 grid(unsigned(ny < 65535 ? ny : 65535));
+    return launch_pdl(k_v2_rhs_x<T, KEEP>, grid, dim3(unsigned(threads)), st, up, dp, u, co[0],
+                      co[1], co[2], co[3], co[5], w, nx, ny, vec_u);
+}
+
 template <typename T>
 static void grid2(int nx, int ny, dim3 &g, dim3 &b) {
     b = dim3(256);
@@ -353,35 +510,44 @@ template <typename T>
 static trid_status v2_forward_step(T *u, T *dw, const T *const co[6], const int64_t *dims,
                                    char *scr, size_t scr_bytes, trid_dtype dt, cudaStream_t st) {
     const int nx = int(dims[0]), ny = int(dims[1]);
-    dim3 g, b;
-    grid2<T>(nx, ny, g, b);
-    if (!launch_pdl(k_v2_rhs<T>, g, b, st, u, co[0], co[2], co[3], co[5], dw, nx, ny))
-        return TRID_ERR_CUDA;
-    trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], dw, nullptr, dims, 2, 0, dt, scr,
-                                        scr_bytes, st);
-    if (s != TRID_OK) return s;
+    if (v2x_fits(nx)) {  // w = X^{-1} d, d formed on the fly
+        if (!launch_v2x<T, false>(nullptr, nullptr, u, co, dw, nx, ny, st)) return TRID_ERR_CUDA;
+    } else {
+        dim3 g, b;
+        grid2<T>(nx, ny, g, b);
+        if (!launch_pdl(k_v2_rhs<T>, g, b, st, u, co[0], co[2], co[3], co[5], dw, nx, ny))
+            return TRID_ERR_CUDA;
+        const trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], dw, nullptr, dims, 2, 0,
+                                                  dt, scr, scr_bytes, st);
+        if (s != TRID_OK) return s;
+    }
     // u += Y^{-1} w
     return trid_solve_batch_ws(co[3], co[4], co[5], dw, u, dims, 2, 1, dt, scr, scr_bytes, st);
 }
 
 // A step recomputed by the backward, keeping u (at u; formed from the
 // previous state up and increment dp unless dp is NULL), w = X^{-1} d (at w)
-// and delta = Y^{-1} w (at dl).  Three launches: the explicit part (which also
-// writes u), the x solve in place, the y solve stored into dl (w stays
-// intact).  u + delta is formed by the next step's first kernel, with the
+// and delta = Y^{-1} w (at dl).  The explicit part (which also writes u) and
+// the x solve (one fused launch for lines of up to 1024 points), then the y
+// solve stored into dl (w stays intact).  u + delta is formed by the next step's first kernel, with the
 // same rounding as the forward's accumulating y solve.
 template <typename T>
 static trid_status v2_recompute_step(const T *up, const T *dp, T *u, T *w, T *dl,
                                      const T *const co[6], const int64_t *dims, char *scr,
                                      size_t scr_bytes, trid_dtype dt, cudaStream_t st) {
     const int nx = int(dims[0]), ny = int(dims[1]);
-    dim3 g, b;
-    grid2<T>(nx, ny, g, b);
-    if (!launch_pdl(k_v2_rhs_keep<T>, g, b, st, up, dp, u, co[0], co[2], co[3], co[5], w, nx, ny))
-        return TRID_ERR_CUDA;
-    trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], w, nullptr, dims, 2, 0, dt, scr,
-                                        scr_bytes, st);
-    if (s != TRID_OK) return s;
+    if (v2x_fits(nx)) {  // the same fused kernel as the forward, u formed on the fly
+        if (!launch_v2x<T, true>(up, dp, u, co, w, nx, ny, st)) return TRID_ERR_CUDA;
+    } else {
+        dim3 g, b;
+        grid2<T>(nx, ny, g, b);
+        if (!launch_pdl(k_v2_rhs_keep<T>, g, b, st, up, dp, u, co[0], co[2], co[3], co[5], w, nx,
+                        ny))
+            return TRID_ERR_CUDA;
+        const trid_status s = trid_solve_batch_ws(co[0], co[1], co[2], w, nullptr, dims, 2, 0, dt,
+                                                  scr, scr_bytes, st);
+        if (s != TRID_OK) return s;
+    }
     return solve_into_ws(co[3], co[4], co[5], w, dl, dims, 2, 1, dt, scr, scr_bytes, st);
 }
 

@@ -48,8 +48,12 @@ def gpu_run(u0, kap, tg, dims, lam, steps, every, dtype, want_coef=False):
             gc.cpu().numpy() if gc is not None else None)
 
 
+# Lines of nx a multiple of 8 up to 1024 take the fused explicit-part + x-solve
+# kernel (64, 128, 16 and the 1024^2 case below), the others the separate
+# kernels (33, 300, 17, 3 and 1032, just past the fused kernel's limit).
 CASES = [((33, 20), 0.3, 5, 2), ((64, 48), 0.2, 12, 5), ((300, 40), 0.25, 4, 3),
-         ((17, 260), 0.2, 3, 10), ((3, 3), 0.2, 2, 1), ((128, 128), 0.2, 50, 10)]
+         ((17, 260), 0.2, 3, 10), ((3, 3), 0.2, 2, 1), ((128, 128), 0.2, 50, 10),
+         ((16, 24), 0.2, 6, 4), ((1032, 12), 0.2, 3, 2)]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
@@ -85,6 +89,29 @@ def test_checkpoint_spacing_does_not_change_the_gradient(dtype):
             else:
                 for a, b in zip(got, ref):
                     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+def test_unaligned_state_gives_the_same_bits(dtype):
+    """The fused line kernel reads the caller's u with scalar loads when it is
+    not on a 16-byte boundary: the same arithmetic, so the same bits as an
+    aligned buffer, forward and gradients."""
+    dims, lam, steps, every = (64, 40), 0.2, 9, 4
+    u0, kap, tg = problem(dims, 31, dtype)
+    n = dims[0] * dims[1]
+    tu, tk, tt = (dev(v, dtype) for v in (u0, kap, tg))
+    outs = []
+    for shift in (0, 1):
+        big = torch.empty(n + 2, dtype=DT[dtype], device="cuda")
+        uT_buf = big[shift:shift + n]
+        assert (uT_buf.data_ptr() % 16 == 0) == (shift == 0)
+        uT, ck = trid.adi2v_forward(tu, tk, dims, lam, steps, every, uT=uT_buf)
+        g = 2.0 * (uT - tt) / n
+        gu, gk, _ = trid.adi2v_backward(g, tk, dims, lam, steps, every, ck)
+        torch.cuda.synchronize()
+        outs.append([x.cpu().numpy() for x in (uT, gu, gk)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
 
 
 def test_autograd_matches_direct_calls():
