@@ -16,10 +16,12 @@
 //     L   (> 4088 rows)  one system per block, two passes: pass 1 reads the
 //                        system and writes the two reduced rows of every
 //                        M-row tile to shared memory; the reduced system is
-//                        reduced again in shared memory until one warp can
-//                        solve it, and substituted back level by level; pass 2
-//                        re-reads the system (L2-resident), repeats the tile
-//                        pass and writes x.
+//                        reduced again in shared memory until it has at most
+//                        two rows per thread, solved there by block-wide PCR
+//                        (stopping once the couplings are below 1/16 ulp) and
+//                        substituted back level by level; pass 2 re-reads the
+//                        system (L2-resident), repeats the tile pass and
+//                        writes x.
 //     M2  (<= 4088)      one system per block, one pass: every thread keeps
 //                        its tile in registers through the reduced solve.
 //     M1  (<= 1016)      one system per team of 4 warps (4 teams per block,
